@@ -1,0 +1,322 @@
+#!/usr/bin/env python3
+"""Benchmark: EOFA CG time-to-1e-10 on one GB300 (and replicas on N GPUs).
+
+Workload (one step = one solve H_T(m, m) x = b to an FP64 true residual of 1e-10):
+  16^3 x 32 lattice, Ns = 16 optimal domain-wall weights (Zolotarev, lambda in [0.05, 6.2]),
+  m0 = 1.3, normalised mass m = 0.01, seeded SU(3) links U = exp(i 0.3 sum lambda^a r^a),
+  Gaussian 5D right-hand side b. Inputs are synthetic (the paper's thermalised ensembles are
+  not available). The chosen method (FP32 or FP16-storage inner CGNE with FP64 reliable updates)
+  is timed; the plain FP64 GPU CGNE on the same system is timed once beside it.
+
+Output: one JSON line (rank 0). `value` = seconds per solve over the whole job (K solves per
+rank, all ranks, max-over-ranks wall time / total solves). Multi-GPU runs are independent
+replicas (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import resource
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "EOFA CG time-to-1e-10 (chosen vs plain FP64 on GPU); dslash HBM GB/s"
+WORKLOAD = {"workload": "16^3x32 Ns=16 optimal DWF (Zolotarev omega on [0.05,6.2]), m0=1.3, m=0.01, "
+                        "links eps=0.3, H_T(m,m) x = b to true residual 1e-10",
+            "dims": [16, 16, 16, 32], "Ns": 16, "m0": 1.3, "mass": 0.01, "tol": 1e-10}
+DIMS, NS, M0, MASS, EPS, TOL = (16, 16, 16, 32), 16, 1.3, 0.01, 0.3, 1e-10
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                if out.returncode == 0 and out.stdout.strip():
+                    self.samples.append([x.strip() for x in out.stdout.strip().split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if len(s) > 5 + i and s[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# algorithmic bytes per launch of the fused hopping kernels (per 5D half-site: spinor reads and
+# writes of 24 reals, links 8 x 18 reals per 4D half-site shared by Ns slices)
+def alg_bytes(key, Vh, Ns):
+    st = key // 100000
+    hop, mixhop, own, mixown, epi = (key // 10000) % 10, (key // 1000) % 10, (key // 100) % 10, (key // 10) % 10, key % 10
+    rb = {0: 8, 1: 4, 2: 2}[st]        # bytes per real of the spinor storage
+    lb = 8 if st == 0 else 4           # link storage
+    scale = 4 if st == 2 else 0        # FP16 per-site scale per field access
+    n5 = Vh * Ns
+    fields = 0
+    if hop:
+        fields += 1                    # the hopped field, read once from HBM
+    if own:
+        fields += 1
+    fields += 1                        # output (or updated field) write
+    if epi == 2:                       # CG_A: read x, r; write x, r (own = p already read)
+        fields += 3
+    elif epi == 3:                     # CG_B: read p (output writes p)
+        fields += 1
+    elif epi == 4:                     # RESID: read b
+        fields += 1
+    by = n5 * fields * (24 * rb + scale)
+    if hop:
+        by += Vh * 8 * 18 * lb
+    return by
+
+
+def kernel_name(key):
+    st = ["fp64", "fp32", "fp16"][key // 100000]
+    hop, mixhop, own, mixown, epi = (key // 10000) % 10, (key // 1000) % 10, (key // 100) % 10, (key // 10) % 10, key % 10
+    kind = {(1, 1, 0, 0): "hop+A^-1", (1, 0, 1, 1): "hop+A*own", (1, 1, 1, 0): "hop+own+A^-1",
+            (1, 0, 1, 0): "hop+own", (0, 0, 1, 1): "s-mix"}.get((hop, mixhop, own, mixown), "hop")
+    epin = ["store", "store+norm", "cg_a", "cg_b", "resid"][epi]
+    return f"k_hop<{st},{kind},{epin}>"
+
+
+def cpu_oracle_sample(n_full_iters):
+    """Oracle CGNE iteration timed on a 16^3 x 4 slab of the workload (1/8 of its volume), scaled
+    by volume to the full lattice and multiplied by the GPU FP64 CGNE iteration count."""
+    import numpy as np
+    from oracle.operators import ODWF as OO
+    from oracle import solver as osol
+    from paper_1710_09621_gb300 import inputs
+    dims = (16, 16, 16, 4)
+    U = inputs.random_su3_links(dims, EPS, inputs.seed_for(1, 7))
+    op = OO(U, M0, inputs.omega_zolotarev(NS, 0.05, 6.2))
+    sch = osol.Schur(op, MASS, MASS)
+    b = inputs.gaussian_spinor5(dims, NS, inputs.seed_for(1, 8)) * sch.even
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
+    t0 = time.perf_counter()
+    osol.cgne(sch.S, sch.S_dag, b, 0.0, 1)   # one CGNE iteration: S^dag (init) + S + S^dag
+    wall = time.perf_counter() - t0
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
+    # the sample ran 3 Schur applies; one iteration is 2
+    t_iter_full = wall * (2.0 / 3.0) * 8.0
+    return {"t_iter_full_s": t_iter_full, "wall_s": wall, "cores": max(1, round(cpu / wall)) if wall > 0 else 1,
+            "value": t_iter_full * n_full_iters}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step one CGNE iteration on a 16^3 x 4 slab."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n_iters = args.ref_iters
+    times = []
+    for i in range(args.warmup + args.steps):
+        s = cpu_oracle_sample(n_iters)
+        if i >= args.warmup:
+            times.append(s)
+    v = statistics.median([t["value"] for t in times])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * v, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": WORKLOAD,
+            "cpu_baseline": {"kind": "oracle", "value": v, "unit": "s", "cores": times[0]["cores"],
+                             "sample": f"one oracle CGNE iteration per step on a 16^3x4 slab (1/8 volume), "
+                                       f"scaled by volume and by {n_iters} iterations (FP64 CGNE iteration "
+                                       f"count of this workload)"},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="single", choices=["single", "half", "double"])
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--ref-iters", type=int, default=1700)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    from paper_1710_09621_gb300 import build, inputs
+    from paper_1710_09621_gb300.binding import ODWF, solve_opts
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build()
+    dev = torch.device("cuda", local)
+    om = inputs.omega_zolotarev(NS, 0.05, 6.2)
+    U = torch.from_numpy(inputs.random_su3_links(DIMS, EPS, inputs.seed_for(1, rank))).to(dev)
+    b_host = torch.from_numpy(inputs.gaussian_spinor5(DIMS, NS, inputs.seed_for(1, 100 + rank))).pin_memory()
+    b = b_host.to(dev)
+    lat = ODWF(DIMS, NS, M0, om)
+    lat.set_gauge(U)
+    opts = solve_opts(tol=TOL, prec=args.prec)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        x, st = lat.solve(b, MASS, MASS, opts=opts)
+    # ---- timed region: device-resident inputs -------------------------------------------------
+    lat.profile(True)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = []
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            x, st = lat.solve(b, MASS, MASS, x=x, opts=opts)
+            stats.append(st)
+        ev1.record(stream)
+        barrier()
+    prof = lat.profile_read()
+    lat.profile(False)
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    t = torch.tensor([elapsed], device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    elapsed = float(t.item())
+    value = elapsed / (args.steps * world)
+
+    # ---- e2e: pinned host input -> device -> solve -> pinned host output ------------------------
+    x_host = torch.empty_like(b_host).pin_memory()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        bd = b_host.to(dev, non_blocking=True)
+        xd, _ = lat.solve(bd, MASS, MASS, opts=opts)
+        x_host.copy_(xd, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_el = e0.elapsed_time(e1) / 1e3
+    t = torch.tensor([e2e_el], device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = float(t.item()) / (args.steps * world)
+
+    # ---- plain FP64 GPU CGNE on the same system ----------------------------------------------
+    fp64 = None
+    if not args.no_fp64:
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        _, st64 = lat.solve(b, MASS, MASS, opts=solve_opts(tol=TOL, prec="double"))
+        f1.record(stream)
+        barrier()
+        fp64 = {"seconds": f0.elapsed_time(f1) / 1e3, "iters": st64["iters"], "true_residual": st64["true_residual"]}
+
+    # ---- roofline of the dominant kernel -------------------------------------------------------
+    Vh = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] // 2
+    peak, peak_kind = peaks()
+    kern = []
+    for key, (n, ms) in prof.items():
+        avg_s = ms / 1e3 / n
+        by = alg_bytes(key, Vh, NS)
+        kern.append({"kernel": kernel_name(key), "key": key, "launches": n, "total_ms": ms,
+                     "avg_us": avg_s * 1e6, "alg_bytes": by, "gbs": by / avg_s / 1e9})
+    kern.sort(key=lambda k: -k["total_ms"])
+    tot_ms = sum(k["total_ms"] for k in kern) or 1.0
+    for k in kern:
+        k["share"] = k["total_ms"] / tot_ms
+    dom = kern[0] if kern else None
+    roof = None
+    if dom:
+        roof = {"bound": "hbm", "kernel": dom["kernel"], "achieved": dom["gbs"], "peak": peak, "unit": "GB/s",
+                "frac": dom["gbs"] / peak, "peak_source": f"hbm_gbs of {peak_kind}", "traffic": None,
+                "alg_bytes_per_launch": dom["alg_bytes"], "avg_launch_us": dom["avg_us"]}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"single": "f32 (FP64 reliable updates)", "half": "f16 storage/f32 (FP64 reliable updates)",
+                  "double": "f64"}[args.prec],
+        "data": "synthetic",
+        "config": dict(WORKLOAD, prec=args.prec, l2="inputs larger than L2 (each solve streams >1 GB)",
+                       parallelism=f"replicas x{world}"),
+        "solve": {"iters": stats[-1]["iters"], "reliable_updates": stats[-1]["reliable_updates"],
+                  "true_residual": max(s["true_residual"] for s in stats)},
+        "fp64_plain": fp64,
+        "speedup_vs_fp64": (fp64["seconds"] / value) if fp64 else None,
+        "roofline": roof,
+        "kernels": kern,
+        "e2e": {"value": e2e_value, "unit": "s", "h2d_bytes_per_step": b_host.numel() * 16,
+                "d2h_bytes_per_step": x_host.numel() * 16},
+        "gpu_launches": int(sum(k["launches"] for k in kern)),
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu and world == 1:
+        n_it = fp64["iters"] if fp64 else args.ref_iters
+        s = cpu_oracle_sample(n_it)
+        line["cpu_baseline"] = {"value": s["value"], "unit": "s", "cores": s["cores"], "kind": "oracle",
+                                "sample": f"one oracle CGNE iteration on a 16^3x4 slab (1/8 volume, "
+                                          f"{s['wall_s']:.1f} s), scaled by volume and by {n_it} "
+                                          f"FP64 CGNE iterations (estimated)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

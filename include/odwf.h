@@ -1,0 +1,159 @@
+/*
+ * odwf.h -- C ABI of the GB300 library for the exact one-flavor action (EOFA) of optimal
+ * domain-wall fermions with mass preconditioning.
+ *
+ * Paper: Y.-C. Chen and T.-W. Chiu, "Mass Preconditioning for the Exact One-Flavor Action in
+ * Lattice QCD with Domain-Wall Fermion", arXiv:1710.09621. Citations below are to its sections
+ * and equation labels, written Eq.(label).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Status: every call returns int; ODWF_OK (0) on success, a negative ODWF_E* code otherwise.
+ *    Nothing is thrown across the ABI. odwf_last_error(h) returns a message for the last failure
+ *    on that handle (odwf_last_error(NULL) for failures of odwf_create).
+ *  - Device pointers: every field argument is a CUDA device pointer owned by the caller, and must
+ *    stay valid until the work queued on `stream` has finished. `stream` is a cudaStream_t passed
+ *    as void* (NULL = the legacy default stream). All library work on a call is queued on that
+ *    stream; calls that return host scalars (action, statistics) synchronise it.
+ *  - Field layout at the ABI: complex128 (interleaved re, im doubles), C order,
+ *      4D spinor   [t][z][y][x][spin 4][color 3]
+ *      5D spinor   [s][t][z][y][x][spin 4][color 3]      s = 0..Ns-1 outermost
+ *      gauge links [mu 4][t][z][y][x][a 3][b 3]          mu = 0..3 for x, y, z, t
+ *    Gamma matrices are in the chiral basis gamma_5 = diag(1, 1, -1, -1): spins 0,1 are P_+,
+ *    spins 2,3 are P_- (the phi_+ / phi_- split after Eq.(H)). Boundary conditions: periodic in
+ *    x, y, z, antiperiodic in t for the fermion fields.
+ *  - Masses are normalised masses m = m_q / m_PV with m_PV = 2 m0 (after Eq.(H), Section 3.1);
+ *    1.0 is the Pauli-Villars mass. Every mass must lie in (0, 1].
+ *  - The library owns its internal workspaces (even-odd copies of the fields in FP64, FP32 and
+ *    FP16, the reordered gauge field, reduction buffers). A handle is not thread-safe.
+ */
+#ifndef ODWF_H
+#define ODWF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define ODWF_OK          0
+#define ODWF_EINVAL     -1   /* bad argument: dims, Ns, masses, omega, null pointer, option   */
+#define ODWF_ENOMEM     -2   /* device or host allocation failed                              */
+#define ODWF_ECUDA      -3   /* a CUDA runtime call or kernel launch failed                   */
+#define ODWF_ENOCONV    -4   /* the solver reached maxiter without meeting the tolerance      */
+#define ODWF_EBREAKDOWN -5   /* Krylov breakdown: <p,p> <= 0 or a NaN/Inf in a reduction      */
+#define ODWF_ETIMEOUT   -6   /* the solver exceeded its wall-clock budget                     */
+
+/* arithmetic of a call */
+#define ODWF_PREC_DOUBLE 0   /* FP64 storage and arithmetic                                    */
+#define ODWF_PREC_SINGLE 1   /* FP32 storage and arithmetic; solves add FP64 reliable updates  */
+#define ODWF_PREC_HALF   2   /* FP16 storage with a per-site scale, FP32 arithmetic            */
+
+/* operator selector of odwf_apply / odwf_apply_dag */
+#define ODWF_OP_DT    0      /* D_T(m1, m2) of Eq.(DTm1m2)                                     */
+#define ODWF_OP_HT    1      /* H_T(m1, m2) = gamma_5 R5 D_T(m1, m2) (after Eq.(m1m2_m3m2))    */
+#define ODWF_OP_DODWF 2      /* D_odwf(m1, m2) = (omega D_w + 1) + (omega D_w - 1) L(m1, m2)   */
+
+typedef struct odwf_s odwf_t;
+
+typedef struct {
+    double tol;          /* stop when ||b' - D_T x|| <= tol ||b'|| (FP64 true residual); e.g. 1e-10 */
+    int    maxiter;      /* Krylov iterations, summed over reliable-update cycles                   */
+    int    prec;         /* ODWF_PREC_*: inner-solver storage precision                             */
+    double delta;        /* reliable-update trigger: |r_inner| < delta * max |r| since last update  */
+    double max_seconds;  /* wall-clock budget; <= 0 means none                                      */
+} odwf_solve_opts;
+
+typedef struct {
+    int    iters;            /* Krylov iterations (each: one Schur apply and one adjoint apply)  */
+    int    reliable_updates; /* FP64 residual replacements                                        */
+    double true_residual;    /* ||b' - D_T x|| / ||b'|| recomputed in FP64 after the solve        */
+    double seconds;          /* host wall time of the call                                        */
+} odwf_solve_stats;
+
+/* One EOFA pseudofermion term, Eq.(m1m2_m3m4) in its two chiral special cases:
+ *   chirality -1: (m3, m4)/(m3, m_den), Eq.(m1m2_m1m4), k = k(m_den, m4)
+ *   chirality +1: (m3, m4)/(m_den, m4), Eq.(m1m2_m3m2), k = k(m_den, m3)
+ * Its 4D operator is X = P [1 -/+ k Omega^T H_T(m3, m4)^{-1} Omega] P and its action phi^dag X phi. */
+typedef struct {
+    int    chirality;
+    double m3, m4, m_den;
+} eofa_term;
+
+typedef struct {
+    odwf_solve_opts solve;   /* options of every pole solve                                       */
+    double x_lo, x_hi;       /* spectral interval of X for the rational approximation of X^{-1/2};
+                                x_lo <= 0 selects [0.98 (1+m_ref)/(1+m_den), 1]                    */
+    double rat_err;          /* target max relative error of the rational approximation (1e-11)   */
+    int    n_poles_out;      /* written: number of poles used                                      */
+    int    iters_out;        /* written: Krylov iterations summed over poles                       */
+} odwf_hb_opts;
+
+/* Create a handle for an Lx x Ly x Lz x Lt lattice (all even, each >= 2) with Ns slices
+ * (even, 2..32), domain-wall height m0 (0 < m0 < 2) and weights omega[Ns] (host, each > 0,
+ * R5-symmetric: omega_s == omega_{Ns-1-s}, which makes H_T Hermitian). The operator is the
+ * optimal domain-wall fermion read with c = 1, d = 0 (m_PV = 2 m0, Section 3.1). flags: 0.
+ * Returns ODWF_EINVAL for bad arguments, ODWF_ECUDA/ENOMEM on device failures. */
+int odwf_create(odwf_t** h, const int dims[4], int Ns, double m0, const double* omega, int flags);
+int odwf_destroy(odwf_t* h);
+const char* odwf_last_error(const odwf_t* h);
+
+/* Load the gauge field U (device, [4][V][3][3] complex128, unitary). The library keeps even-odd
+ * reordered FP64, FP32 and FP16 copies with the antiperiodic sign folded in; U may be freed after
+ * the stream reaches this point. Must be called before any operator, solve or EOFA call. */
+int odwf_set_gauge(odwf_t* h, const void* U, void* stream);
+
+/* out = Op(m1, m2) in, or its adjoint, on full 5D fields (device, complex128, ABI layout).
+ * op: ODWF_OP_*. prec: ODWF_PREC_DOUBLE or ODWF_PREC_SINGLE (arithmetic of the hopping and
+ * fifth-dimension kernels; in/out stay FP64). in and out must not overlap. */
+int odwf_apply(odwf_t* h, int op, double m1, double m2, const void* in, void* out, int prec, void* stream);
+int odwf_apply_dag(odwf_t* h, int op, double m1, double m2, const void* in, void* out, int prec, void* stream);
+
+/* Solve H_T(m1, m2) x = b (5D, device, complex128), the system behind every EOFA heat-bath,
+ * action and force (Eq.(m1m2_m1m4), Eq.(m1m2_m3m2)); CG is the paper's solver (Section 1).
+ * Method: D_T x = R5 gamma_5 b, even-odd Schur complement S = A - 1/4 H_eo A^{-1} H_oe, CGNE on S,
+ * inner precision opts->prec with FP64 reliable updates, FP64 true residual at the end.
+ * opts may be NULL (tol 1e-10, maxiter 100000, FP64, delta 0.1). stats may be NULL.
+ * Returns ODWF_ENOCONV / EBREAKDOWN / ETIMEOUT when the tolerance is not met (x holds the last
+ * iterate). Synchronises `stream`. */
+int eofa_solve(odwf_t* h, double m1, double m2, const void* b, void* x,
+               const odwf_solve_opts* opts, odwf_solve_stats* stats, void* stream);
+
+/* n independent solves H_T(m12[2i], m12[2i+1]) x[i] = b[i] on the same gauge field, with the
+ * Krylov iterations of all systems interleaved on one stream (each kernel launch covers every
+ * active system). stats: array of n (may be NULL). */
+int eofa_solve_batch(odwf_t* h, int n, const double* m12, const void* const* b, void* const* x,
+                     const odwf_solve_opts* opts, odwf_solve_stats* stats, void* stream);
+
+/* S = phi^dag X phi for one term (phi: 4D device field; only the term's chirality is read).
+ * Written to *S_host. stats (may be NULL) receives the solve's statistics. */
+int eofa_action(odwf_t* h, const eofa_term* term, const void* phi, double* S_host,
+                const odwf_solve_opts* opts, odwf_solve_stats* stats, void* stream);
+
+/* F^a_mu(x) = -dS/dw^a for U_mu(x) -> exp(i w^a t^a) U_mu(x), t^a = lambda^a / 2 (Section 1,
+ * Eq.(molecular_U), Eq.(molecular_P)). F: device, double [4][V][8] (mu, lexicographic site, a). */
+int eofa_force(odwf_t* h, const eofa_term* term, const void* phi, double* F,
+               const odwf_solve_opts* opts, odwf_solve_stats* stats, void* stream);
+
+/* Heat-bath phi = X^{-1/2} eta (Eq.(CG_gaussian)) with Zolotarev's optimal rational approximation
+ * of x^{-1/2} on [x_lo, x_hi]; each pole is one shifted-mass H_T solve (Woodbury on Eq.(delta_ij)),
+ * all poles solved as one batch. eta, phi: 4D device fields; phi gets only the term's chirality. */
+int eofa_heatbath(odwf_t* h, const eofa_term* term, const void* eta, void* phi,
+                  odwf_hb_opts* opts, void* stream);
+
+/* Kernel timing for measurement: while enabled, every launch of the fused hopping kernels is
+ * bracketed by CUDA events on its stream. odwf_profile_read synchronises the device and returns,
+ * per kernel variant seen since the last enable, its key (storage*100000 + hop*10000 +
+ * mixhop*1000 + own*100 + mixown*10 + epilogue), the number of launches and the summed event time
+ * in milliseconds; n_io is the capacity of the arrays on entry and the number of variants on exit.
+ * The paper has no counterpart: this is instrumentation. */
+int odwf_profile_enable(odwf_t* h, int enable);
+int odwf_profile_read(odwf_t* h, int* keys, int* launches, double* total_ms, int* n_io);
+
+/* k(m_j, m_i) of Eq.(k_ij) (c = 1, lambda = 0) and Omega_pm of Eq.(delta_ij) (host, out[Ns]). */
+double eofa_k(double mj, double mi);
+int    odwf_omega_vector(const odwf_t* h, int chirality, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ODWF_H */

@@ -79,3 +79,38 @@ def dense(apply, shape):
         e[j] = 1.0
         cols.append(apply(e.reshape(shape)).reshape(n))
     return np.stack(cols, axis=1)
+
+
+def dt_at_sites(op: ODWF, psi, m1, m2, sites):
+    """(D_T(m1, m2) psi)(x, s) for a list of (s, t, z, y, x) points, one at a time (Eq.(DTm1m2)).
+
+    For checks at lattice sizes where a whole-lattice apply is too slow: each output is the
+    site term, the eight nearest-neighbour hops of D_w and the fifth-dimension sum of M_pm.
+    """
+    from .wilson import GAMMA
+    Mp, Mm = op.m_pair(m1, m2)
+    Lx, Ly, Lz, Lt = op.dims
+    L = {0: Lx, 1: Ly, 2: Lz, 3: Lt}
+    out = []
+    one = np.eye(4)
+    for (s, t, z, y, x) in sites:
+        c = [x, y, z, t]
+        v = (4.0 - op.m0) * psi[s, t, z, y, x]
+        for mu in range(4):
+            f = list(c)
+            f[mu] = (c[mu] + 1) % L[mu]
+            b = list(c)
+            b[mu] = (c[mu] - 1) % L[mu]
+            sf = -1.0 if (mu == 3 and c[3] == Lt - 1) else 1.0
+            sb = -1.0 if (mu == 3 and c[3] == 0) else 1.0
+            Uf = op.U[mu, t, z, y, x]
+            Ub = op.U[mu, b[3], b[2], b[1], b[0]]
+            pf = sf * psi[s, f[3], f[2], f[1], f[0]]
+            pb = sb * psi[s, b[3], b[2], b[1], b[0]]
+            v = v - 0.5 * ((one - GAMMA[mu]) @ (pf @ Uf.T) + (one + GAMMA[mu]) @ (pb @ Ub.conj()))
+        col = psi[:, t, z, y, x]  # (Ns, 4, 3)
+        v = v.copy()
+        v[0:2] += np.einsum("t,tic->ic", Mp[s], col[:, 0:2])
+        v[2:4] += np.einsum("t,tic->ic", Mm[s], col[:, 2:4])
+        out.append(v)
+    return np.array(out)

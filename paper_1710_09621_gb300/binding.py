@@ -1,0 +1,265 @@
+"""Thin ctypes binding of libodwf.so (argument marshalling only).
+
+Every step of the hot path runs in the library's CUDA kernels; this module converts torch
+tensors to device pointers and streams, checks shapes and dtypes, and turns status codes into
+exceptions. There is no CPU fallback: if the library is missing or no GPU is present the calls
+raise.
+
+Field tensors are torch.complex128 CUDA tensors in the ABI layout (see include/odwf.h):
+  links (4, Lt, Lz, Ly, Lx, 3, 3), 4D spinor (Lt, Lz, Ly, Lx, 4, 3),
+  5D spinor (Ns, Lt, Lz, Ly, Lx, 4, 3), force (4, Lt, Lz, Ly, Lx, 8) float64.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libodwf.so")
+
+ODWF_OK, ODWF_EINVAL, ODWF_ENOMEM, ODWF_ECUDA, ODWF_ENOCONV, ODWF_EBREAKDOWN, ODWF_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+PREC_DOUBLE, PREC_SINGLE, PREC_HALF = 0, 1, 2
+OP_DT, OP_HT, OP_DODWF = 0, 1, 2
+_PREC = {"double": PREC_DOUBLE, "single": PREC_SINGLE, "half": PREC_HALF,
+         PREC_DOUBLE: PREC_DOUBLE, PREC_SINGLE: PREC_SINGLE, PREC_HALF: PREC_HALF}
+_OP = {"dt": OP_DT, "ht": OP_HT, "dodwf": OP_DODWF, OP_DT: OP_DT, OP_HT: OP_HT, OP_DODWF: OP_DODWF}
+
+# every entry point the C ABI declares
+EXPORTS = ["odwf_create", "odwf_destroy", "odwf_last_error", "odwf_set_gauge", "odwf_apply", "odwf_apply_dag",
+           "eofa_solve", "eofa_solve_batch", "eofa_action", "eofa_force", "eofa_heatbath", "eofa_k",
+           "odwf_omega_vector", "odwf_profile_enable", "odwf_profile_read"]
+
+
+class OdwfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"odwf error {code}: {msg}")
+        self.code = code
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("prec", ctypes.c_int),
+                ("delta", ctypes.c_double), ("max_seconds", ctypes.c_double)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int),
+                ("true_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"iters": self.iters, "reliable_updates": self.reliable_updates,
+                "true_residual": self.true_residual, "seconds": self.seconds}
+
+
+class Term(ctypes.Structure):
+    _fields_ = [("chirality", ctypes.c_int), ("m3", ctypes.c_double), ("m4", ctypes.c_double),
+                ("m_den", ctypes.c_double)]
+
+
+class HbOpts(ctypes.Structure):
+    _fields_ = [("solve", SolveOpts), ("x_lo", ctypes.c_double), ("x_hi", ctypes.c_double),
+                ("rat_err", ctypes.c_double), ("n_poles_out", ctypes.c_int), ("iters_out", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libodwf.so once; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} not found: build it with `python -m paper_1710_09621_gb300.build`")
+    lib = ctypes.CDLL(path)
+    vp, dp, ip, d, i = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.c_int
+    lib.odwf_create.argtypes = [ctypes.POINTER(vp), ip, i, d, dp, i]
+    lib.odwf_destroy.argtypes = [vp]
+    lib.odwf_last_error.argtypes = [vp]
+    lib.odwf_last_error.restype = ctypes.c_char_p
+    lib.odwf_set_gauge.argtypes = [vp, vp, vp]
+    lib.odwf_apply.argtypes = [vp, i, d, d, vp, vp, i, vp]
+    lib.odwf_apply_dag.argtypes = [vp, i, d, d, vp, vp, i, vp]
+    lib.eofa_solve.argtypes = [vp, d, d, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), vp]
+    lib.eofa_solve_batch.argtypes = [vp, i, dp, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                     ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), vp]
+    lib.eofa_action.argtypes = [vp, ctypes.POINTER(Term), vp, dp, ctypes.POINTER(SolveOpts),
+                                ctypes.POINTER(SolveStats), vp]
+    lib.eofa_force.argtypes = [vp, ctypes.POINTER(Term), vp, vp, ctypes.POINTER(SolveOpts),
+                               ctypes.POINTER(SolveStats), vp]
+    lib.eofa_heatbath.argtypes = [vp, ctypes.POINTER(Term), vp, vp, ctypes.POINTER(HbOpts), vp]
+    lib.eofa_k.argtypes = [d, d]
+    lib.eofa_k.restype = d
+    lib.odwf_omega_vector.argtypes = [vp, i, dp]
+    lib.odwf_profile_enable.argtypes = [vp, i]
+    lib.odwf_profile_read.argtypes = [vp, ip, ip, dp, ip]
+    _lib = lib
+    return lib
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def solve_opts(tol=1e-10, maxiter=100000, prec="double", delta=0.1, max_seconds=0.0):
+    return SolveOpts(tol, maxiter, _PREC[prec], delta, max_seconds)
+
+
+@dataclass
+class TermSpec:
+    chirality: int
+    m3: float
+    m4: float
+    m_den: float
+
+    def c(self):
+        return Term(int(self.chirality), float(self.m3), float(self.m4), float(self.m_den))
+
+
+class ODWF:
+    """One lattice: dims (Lx, Ly, Lz, Lt), Ns, m0 and the R5-symmetric weights omega_s."""
+
+    def __init__(self, dims, Ns, m0, omega):
+        import numpy as np
+        self.lib = load_library()
+        self.dims = tuple(int(x) for x in dims)
+        self.Ns = int(Ns)
+        self.m0 = float(m0)
+        om = np.ascontiguousarray(np.asarray(omega, dtype=np.float64))
+        if om.shape != (self.Ns,):
+            raise ValueError("omega must have Ns entries")
+        h = ctypes.c_void_p()
+        d = (ctypes.c_int * 4)(*self.dims)
+        rc = self.lib.odwf_create(ctypes.byref(h), d, self.Ns, self.m0,
+                                  om.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0)
+        if rc != 0:
+            raise OdwfError(rc, self.lib.odwf_last_error(None).decode())
+        self.h = h
+        Lx, Ly, Lz, Lt = self.dims
+        self.shape4 = (Lt, Lz, Ly, Lx, 4, 3)
+        self.shape5 = (self.Ns,) + self.shape4
+        self.shape_links = (4, Lt, Lz, Ly, Lx, 3, 3)
+        self.shape_force = (4, Lt, Lz, Ly, Lx, 8)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.odwf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, allow=()):
+        if rc != 0 and rc not in allow:
+            raise OdwfError(rc, self.lib.odwf_last_error(self.h).decode())
+        return rc
+
+    @staticmethod
+    def _field(t, shape, dtype=None):
+        import torch
+        dtype = dtype or torch.complex128
+        if not (t.is_cuda and t.dtype == dtype and t.is_contiguous() and tuple(t.shape) == tuple(shape)):
+            raise ValueError(f"expected contiguous CUDA {dtype} tensor of shape {shape}, got "
+                             f"{t.dtype} {tuple(t.shape)} on {t.device}")
+        return t
+
+    def set_gauge(self, U, stream=None):
+        self._check(self.lib.odwf_set_gauge(self.h, _ptr(self._field(U, self.shape_links)), _stream_ptr(stream)))
+
+    def apply(self, x, m1, m2, op="dt", dag=False, prec="double", out=None, stream=None):
+        import torch
+        self._field(x, self.shape5)
+        out = torch.empty_like(x) if out is None else self._field(out, self.shape5)
+        fn = self.lib.odwf_apply_dag if dag else self.lib.odwf_apply
+        self._check(fn(self.h, _OP[op], float(m1), float(m2), _ptr(x), _ptr(out), _PREC[prec], _stream_ptr(stream)))
+        return out
+
+    def solve(self, b, m1, m2, x=None, opts=None, stream=None, allow_noconv=False):
+        """x = H_T(m1, m2)^{-1} b; returns (x, stats dict)."""
+        import torch
+        self._field(b, self.shape5)
+        x = torch.empty_like(b) if x is None else self._field(x, self.shape5)
+        st = SolveStats()
+        o = opts if opts is not None else solve_opts()
+        rc = self.lib.eofa_solve(self.h, float(m1), float(m2), _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(st),
+                                 _stream_ptr(stream))
+        self._check(rc, allow=(ODWF_ENOCONV,) if allow_noconv else ())
+        d = st.as_dict()
+        d["status"] = rc
+        return x, d
+
+    def solve_batch(self, bs, m12, opts=None, stream=None):
+        import torch
+        n = len(bs)
+        xs = [torch.empty_like(b) for b in bs]
+        for b in bs:
+            self._field(b, self.shape5)
+        arr = (ctypes.c_double * (2 * n))(*[float(v) for pair in m12 for v in pair])
+        bp = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bs])
+        xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+        st = (SolveStats * n)()
+        o = opts if opts is not None else solve_opts()
+        self._check(self.lib.eofa_solve_batch(self.h, n, arr, bp, xp, ctypes.byref(o), st, _stream_ptr(stream)))
+        return xs, [s.as_dict() for s in st]
+
+    def action(self, term: TermSpec, phi, opts=None, stream=None):
+        self._field(phi, self.shape4)
+        S = ctypes.c_double()
+        st = SolveStats()
+        o = opts if opts is not None else solve_opts()
+        t = term.c()
+        self._check(self.lib.eofa_action(self.h, ctypes.byref(t), _ptr(phi), ctypes.byref(S), ctypes.byref(o),
+                                         ctypes.byref(st), _stream_ptr(stream)))
+        return S.value, st.as_dict()
+
+    def force(self, term: TermSpec, phi, opts=None, out=None, stream=None):
+        import torch
+        self._field(phi, self.shape4)
+        F = torch.empty(self.shape_force, dtype=torch.float64, device=phi.device) if out is None else out
+        self._field(F, self.shape_force, torch.float64)
+        st = SolveStats()
+        o = opts if opts is not None else solve_opts()
+        t = term.c()
+        self._check(self.lib.eofa_force(self.h, ctypes.byref(t), _ptr(phi), _ptr(F), ctypes.byref(o),
+                                        ctypes.byref(st), _stream_ptr(stream)))
+        return F, st.as_dict()
+
+    def heatbath(self, term: TermSpec, eta, opts=None, x_lo=0.0, x_hi=1.0, rat_err=1e-11, stream=None):
+        import torch
+        self._field(eta, self.shape4)
+        phi = torch.empty_like(eta)
+        hb = HbOpts(opts if opts is not None else solve_opts(), x_lo, x_hi, rat_err, 0, 0)
+        t = term.c()
+        self._check(self.lib.eofa_heatbath(self.h, ctypes.byref(t), _ptr(eta), _ptr(phi), ctypes.byref(hb),
+                                           _stream_ptr(stream)))
+        return phi, {"n_poles": hb.n_poles_out, "iters": hb.iters_out}
+
+    def profile(self, enable=True):
+        self._check(self.lib.odwf_profile_enable(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{kernel key: (launches, total ms)} of the fused hopping kernels since profile(True)."""
+        n = ctypes.c_int(64)
+        keys = (ctypes.c_int * 64)()
+        cnt = (ctypes.c_int * 64)()
+        ms = (ctypes.c_double * 64)()
+        self._check(self.lib.odwf_profile_read(self.h, keys, cnt, ms, ctypes.byref(n)))
+        return {keys[i]: (cnt[i], ms[i]) for i in range(min(n.value, 64))}
+
+    def omega_vector(self, chirality):
+        out = (ctypes.c_double * self.Ns)()
+        self._check(self.lib.odwf_omega_vector(self.h, int(chirality), out))
+        return list(out)
+
+
+def eofa_k(mj, mi):
+    return load_library().eofa_k(float(mj), float(mi))

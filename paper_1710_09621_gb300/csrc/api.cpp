@@ -1,0 +1,457 @@
+// Handle management, fifth-dimension coefficient setup and the operator applies of the C ABI.
+//
+// The fifth-dimension matrices are the optimal domain-wall ones read with c = 1, d = 0:
+//   M_pm(m) = omega^{-1/2} (1 - L_pm(m)) (1 + L_pm(m))^{-1} omega^{-1/2}      (Eq.(DTm1m2) blocks)
+//   (L_+)_{s,s-1} = 1 (s >= 1), (L_+)_{0,Ns-1} = -m, L_- = L_+^T
+// and the even-odd diagonal block is A_pm = (4 - m0) + M_pm. They are computed once per mass pair
+// on the host in FP64 (Ns x Ns, negligible work) and uploaded transposed for the kernels.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "odwf_internal.h"
+
+using namespace odwf;
+
+namespace odwf {
+
+int spb_for(int Ns);
+int solve_core(odwf_s* h, double m1, double m2, const odwf_solve_opts* opts, odwf_solve_stats* stats,
+               cudaStream_t st);
+
+static std::string g_create_err;
+
+int set_err(odwf_s* h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    else g_create_err = msg;
+    return code;
+}
+
+int cuda_check(odwf_s* h, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return ODWF_OK;
+    return set_err(h, ODWF_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// ---- small dense FP64 linear algebra on the host (Ns <= 32) ------------------------------------
+using Mat = std::vector<double>;  // row-major Ns x Ns
+
+static Mat mat_eye(int n) {
+    Mat m(n * n, 0.0);
+    for (int i = 0; i < n; ++i) m[i * n + i] = 1.0;
+    return m;
+}
+
+static Mat mat_mul(const Mat& a, const Mat& b, int n) {
+    Mat c(n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) {
+            const double aik = a[i * n + k];
+            if (aik == 0.0) continue;
+            for (int j = 0; j < n; ++j) c[i * n + j] += aik * b[k * n + j];
+        }
+    return c;
+}
+
+// Gauss-Jordan elimination with partial pivoting; returns false if singular.
+static bool mat_inv(const Mat& a, Mat& inv, int n) {
+    Mat w = a;
+    inv = mat_eye(n);
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < n; ++r)
+            if (std::fabs(w[r * n + col]) > std::fabs(w[piv * n + col])) piv = r;
+        if (w[piv * n + col] == 0.0) return false;
+        if (piv != col)
+            for (int j = 0; j < n; ++j) {
+                std::swap(w[piv * n + j], w[col * n + j]);
+                std::swap(inv[piv * n + j], inv[col * n + j]);
+            }
+        const double d = 1.0 / w[col * n + col];
+        for (int j = 0; j < n; ++j) {
+            w[col * n + j] *= d;
+            inv[col * n + j] *= d;
+        }
+        for (int r = 0; r < n; ++r) {
+            if (r == col) continue;
+            const double f = w[r * n + col];
+            if (f == 0.0) continue;
+            for (int j = 0; j < n; ++j) {
+                w[r * n + j] -= f * w[col * n + j];
+                inv[r * n + j] -= f * inv[col * n + j];
+            }
+        }
+    }
+    return true;
+}
+
+static Mat transpose(const Mat& a, int n) {
+    Mat t(n * n);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) t[j * n + i] = a[i * n + j];
+    return t;
+}
+
+// M_pm(m) for chirality c = +1 (L_+) or -1 (L_- = L_+^T)
+static bool m_matrix(const std::vector<double>& omega, double m, int c, Mat& M) {
+    const int n = (int)omega.size();
+    Mat L(n * n, 0.0);
+    for (int s = 1; s < n; ++s) L[s * n + (s - 1)] = 1.0;
+    L[0 * n + (n - 1)] = -m;
+    if (c < 0) L = transpose(L, n);
+    Mat onepl = mat_eye(n), oneml = mat_eye(n);
+    for (int i = 0; i < n * n; ++i) {
+        onepl[i] += L[i];
+        oneml[i] -= L[i];
+    }
+    Mat inv;
+    if (!mat_inv(onepl, inv, n)) return false;
+    Mat core = mat_mul(oneml, inv, n);
+    M.assign(n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) M[i * n + j] = core[i * n + j] / std::sqrt(omega[i] * omega[j]);
+    return true;
+}
+
+const SCoef* get_coef(odwf_s* h, double m1, double m2) {
+    auto key = std::make_pair(m1, m2);
+    auto it = h->coefs.find(key);
+    if (it != h->coefs.end()) return &it->second;
+    const int n = h->Ns;
+    Mat Mp, Mm;
+    if (!m_matrix(h->omega, m1, +1, Mp) || !m_matrix(h->omega, m2, -1, Mm)) {
+        set_err(h, ODWF_EINVAL, "singular 1 + L in the fifth-dimension setup");
+        return nullptr;
+    }
+    Mat Ap = Mp, Am = Mm;
+    for (int i = 0; i < n; ++i) {
+        Ap[i * n + i] += 4.0 - h->m0;
+        Am[i * n + i] += 4.0 - h->m0;
+    }
+    Mat Api, Ami;
+    if (!mat_inv(Ap, Api, n) || !mat_inv(Am, Ami, n)) {
+        set_err(h, ODWF_EINVAL, "singular even-odd diagonal block A");
+        return nullptr;
+    }
+    // order: A+, A-, A+^-1, A-^-1, A+^T, A-^T, A+^-T, A-^-T ; each stored transposed (Mt[s'][s])
+    const Mat* mats[8];
+    Mat ApT = transpose(Ap, n), AmT = transpose(Am, n), ApiT = transpose(Api, n), AmiT = transpose(Ami, n);
+    mats[0] = &Ap; mats[1] = &Am; mats[2] = &Api; mats[3] = &Ami;
+    mats[4] = &ApT; mats[5] = &AmT; mats[6] = &ApiT; mats[7] = &AmiT;
+    std::vector<double> host(8 * n * n);
+    for (int k = 0; k < 8; ++k) {
+        Mat t = transpose(*mats[k], n);
+        std::memcpy(host.data() + (size_t)k * n * n, t.data(), sizeof(double) * n * n);
+    }
+    SCoef c;
+    if (cudaMalloc(&c.dev, sizeof(double) * host.size()) != cudaSuccess) {
+        set_err(h, ODWF_ENOMEM, "cudaMalloc coefficients");
+        return nullptr;
+    }
+    if (cudaMemcpy(c.dev, host.data(), sizeof(double) * host.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(c.dev);
+        set_err(h, ODWF_ECUDA, "cudaMemcpy coefficients");
+        return nullptr;
+    }
+    auto res = h->coefs.emplace(key, c);
+    return &res.first->second;
+}
+
+static int alloc(odwf_s* h, void** p, size_t bytes) {
+    if (*p) return ODWF_OK;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        *p = nullptr;
+        return set_err(h, ODWF_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    return ODWF_OK;
+}
+
+int ensure_workspace(odwf_s* h, int inner) {
+    Workspace& w = h->ws;
+    const size_t b64 = half_elems_bytes(h, ST_DOUBLE);
+    int rc;
+    void** f64s[] = {&w.b_e, &w.b_o, &w.x_e, &w.x_o, &w.r64, &w.t64, &w.bh};
+    for (void** p : f64s)
+        if ((rc = alloc(h, p, b64))) return rc;
+    // inner-solver fields, sized for the widest storage requested so far
+    const size_t bi = half_elems_bytes(h, inner == ST_HALF ? ST_FLOAT : inner);
+    if (bi > w.inner_bytes) {
+        void** fis[] = {&w.xi, &w.ri, &w.pi, &w.ti};
+        for (void** p : fis) {
+            cudaFree(*p);
+            *p = nullptr;
+            if ((rc = alloc(h, p, bi))) return rc;
+        }
+        w.inner_bytes = bi;
+    }
+    if (inner == ST_HALF) {
+        const size_t bs = (size_t)h->Vh * h->Ns * sizeof(float);
+        void** scs[] = {(void**)&w.xi_s, (void**)&w.ri_s, (void**)&w.pi_s, (void**)&w.ti_s};
+        for (void** p : scs)
+            if ((rc = alloc(h, p, bs))) return rc;
+    }
+    return ODWF_OK;
+}
+
+}  // namespace odwf
+
+// ================================================================================================
+extern "C" {
+
+const char* odwf_last_error(const odwf_t* h) { return h ? h->err.c_str() : odwf::g_create_err.c_str(); }
+
+double eofa_k(double mj, double mi) { return 2.0 * (mj - mi) / ((1.0 + mj) * (1.0 + mi)); }
+
+int odwf_create(odwf_t** out, const int dims[4], int Ns, double m0, const double* omega, int flags) {
+    if (!out || !dims || !omega) return set_err(nullptr, ODWF_EINVAL, "null argument");
+    *out = nullptr;
+    (void)flags;
+    for (int i = 0; i < 4; ++i)
+        if (dims[i] < 2 || dims[i] % 2) return set_err(nullptr, ODWF_EINVAL, "every lattice extent must be even and >= 2");
+    if (Ns < 2 || Ns % 2 || Ns > kMaxNs || spb_for(Ns) * Ns > 256)
+        return set_err(nullptr, ODWF_EINVAL, "Ns must be even, <= 32 and not 18, 22, 26 or 30");
+    if (!(m0 > 0.0 && m0 < 2.0)) return set_err(nullptr, ODWF_EINVAL, "m0 must lie in (0, 2)");
+    for (int s = 0; s < Ns; ++s) {
+        if (!(omega[s] > 0.0) || !std::isfinite(omega[s])) return set_err(nullptr, ODWF_EINVAL, "omega_s must be > 0");
+        if (omega[s] != omega[Ns - 1 - s])
+            return set_err(nullptr, ODWF_EINVAL, "omega must be R5-symmetric (omega_s == omega_{Ns-1-s})");
+    }
+    const long long V = (long long)dims[0] * dims[1] * dims[2] * dims[3];
+    if (V * Ns * 12 > (1LL << 40) || V > (1LL << 30)) return set_err(nullptr, ODWF_EINVAL, "lattice too large");
+    odwf_s* h = new odwf_s();
+    for (int i = 0; i < 4; ++i) h->L[i] = dims[i];
+    h->V = (int)V;
+    h->Vh = (int)(V / 2);
+    h->Ns = Ns;
+    h->m0 = m0;
+    h->omega.assign(omega, omega + Ns);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        std::string msg = std::string("no CUDA device: ") + cudaGetErrorString(e);
+        delete h;
+        return set_err(nullptr, ODWF_ECUDA, msg);
+    }
+    // geometry tables (host-built, uploaded once)
+    const int Lx = dims[0], Ly = dims[1], Lz = dims[2], Lt = dims[3];
+    std::vector<int> lexof[2], cbof(V), nbr[2];
+    for (int p = 0; p < 2; ++p) {
+        lexof[p].resize(h->Vh);
+        nbr[p].resize((size_t)h->Vh * 8);
+    }
+    for (int lex = 0; lex < V; ++lex) {
+        const int x = lex % Lx, y = (lex / Lx) % Ly, z = (lex / (Lx * Ly)) % Lz, t = lex / (Lx * Ly * Lz);
+        const int p = (x + y + z + t) & 1;
+        lexof[p][lex / 2] = lex;
+        cbof[lex] = lex / 2;
+    }
+    for (int p = 0; p < 2; ++p)
+        for (int cb = 0; cb < h->Vh; ++cb) {
+            const int lex = lexof[p][cb];
+            int c[4] = {lex % Lx, (lex / Lx) % Ly, (lex / (Lx * Ly)) % Lz, lex / (Lx * Ly * Lz)};
+            const int L[4] = {Lx, Ly, Lz, Lt};
+            for (int mu = 0; mu < 4; ++mu) {
+                int f[4] = {c[0], c[1], c[2], c[3]}, b[4] = {c[0], c[1], c[2], c[3]};
+                f[mu] = (f[mu] + 1) % L[mu];
+                b[mu] = (b[mu] + L[mu] - 1) % L[mu];
+                const int lf = f[0] + Lx * (f[1] + Ly * (f[2] + Lz * f[3]));
+                const int lb = b[0] + Lx * (b[1] + Ly * (b[2] + Lz * b[3]));
+                nbr[p][(size_t)cb * 8 + mu] = cbof[lf];
+                nbr[p][(size_t)cb * 8 + 4 + mu] = cbof[lb];
+            }
+        }
+    int rc = ODWF_OK;
+    for (int p = 0; p < 2 && !rc; ++p) {
+        rc = alloc(h, (void**)&h->lexof[p], sizeof(int) * h->Vh);
+        if (!rc) rc = alloc(h, (void**)&h->nbr[p], sizeof(int) * 8 * (size_t)h->Vh);
+        if (!rc) rc = alloc(h, (void**)&h->U64[p], sizeof(double) * 8 * 18 * (size_t)h->Vh);
+        if (!rc) rc = alloc(h, (void**)&h->U32[p], sizeof(float) * 8 * 20 * (size_t)h->Vh);
+        if (!rc) rc = cuda_check(h, cudaMemcpy(h->lexof[p], lexof[p].data(), sizeof(int) * h->Vh, cudaMemcpyHostToDevice), "upload lexof");
+        if (!rc) rc = cuda_check(h, cudaMemcpy(h->nbr[p], nbr[p].data(), sizeof(int) * 8 * (size_t)h->Vh, cudaMemcpyHostToDevice), "upload nbr");
+    }
+    h->partials_n = h->num_sms * 32;
+    if (!rc) rc = alloc(h, (void**)&h->partials, sizeof(double) * h->partials_n);
+    if (!rc) rc = alloc(h, (void**)&h->state, sizeof(CGState));
+    if (!rc) rc = cuda_check(h, cudaMemset(h->state, 0, sizeof(CGState)), "memset state");
+    if (!rc) rc = cuda_check(h, cudaMallocHost((void**)&h->state_host, sizeof(CGState)), "cudaMallocHost state");
+    if (rc) {
+        std::string msg = h->err;
+        odwf_destroy(h);
+        return set_err(nullptr, rc, msg);
+    }
+    *out = h;
+    return ODWF_OK;
+}
+
+int odwf_destroy(odwf_t* h) {
+    if (!h) return ODWF_OK;
+    for (int p = 0; p < 2; ++p) {
+        cudaFree(h->nbr[p]);
+        cudaFree(h->lexof[p]);
+        cudaFree(h->U64[p]);
+        cudaFree(h->U32[p]);
+    }
+    for (auto& kv : h->coefs) cudaFree(kv.second.dev);
+    for (auto& r : h->prof_recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : h->prof_pool) cudaEventDestroy(e);
+    cudaFree(h->partials);
+    cudaFree(h->state);
+    if (h->state_host) cudaFreeHost(h->state_host);
+    Workspace& w = h->ws;
+    void* ps[] = {w.b_e, w.b_o, w.x_e, w.x_o, w.r64, w.t64, w.bh, w.xi, w.ri, w.pi, w.ti,
+                  w.xi_s, w.ri_s, w.pi_s, w.ti_s, h->f64[0], h->f64[1], h->f64[2], h->f64[3], h->acc4};
+    for (void* p : ps) cudaFree(p);
+    delete h;
+    return ODWF_OK;
+}
+
+int odwf_set_gauge(odwf_t* h, const void* U, void* stream) {
+    if (!h || !U) return set_err(h, ODWF_EINVAL, "null argument");
+    int rc = launch_gauge(h, (const double*)U, (cudaStream_t)stream);
+    if (!rc) h->have_gauge = true;
+    return rc;
+}
+
+int odwf_omega_vector(const odwf_t* h, int chirality, double* out) {
+    if (!h || !out || (chirality != 1 && chirality != -1)) return ODWF_EINVAL;
+    const int n = h->Ns;
+    for (int s = 0; s < n; ++s) {
+        const int e = chirality < 0 ? s : (n - 1 - s);
+        out[s] = ((e & 1) ? -1.0 : 1.0) / std::sqrt(h->omega[s]);
+    }
+    return ODWF_OK;
+}
+
+}  // extern "C"
+
+// ---- operator applies --------------------------------------------------------------------------
+namespace odwf {
+
+static int check_mass(odwf_s* h, double m) {
+    if (!(m > 0.0 && m <= 1.0)) return set_err(h, ODWF_EINVAL, "masses must lie in (0, 1]");
+    return ODWF_OK;
+}
+
+// out_p = A_p-block(own) - 1/2 H in_{1-p}, i.e. D_T (dagger: with transposed s-matrices and
+// gamma_5 on both sides) for one output parity; storage of the fields: `stg`.
+int apply_dt_parity(odwf_s* h, int stg, const SCoef* c, bool dag, int parity, const void* in_other,
+                    const void* own, void* out, cudaStream_t st) {
+    HopArgs a{};
+    a.in = in_other;
+    a.own = own;
+    a.out = out;
+    a.mown = c->dev + (size_t)(dag ? 4 : 0) * h->Ns * h->Ns;
+    a.c_hop = -0.5;
+    a.g5 = dag ? (G5_HOP_IN | G5_OWN_IN | G5_OUT) : 0;
+    return launch_hop(h, stg, parity, false, true, true, EPI_STORE, a, st);
+}
+
+static int apply_common(odwf_s* h, int op, double m1, double m2, const void* in, void* out, int prec, bool dag,
+                        cudaStream_t st) {
+    if (!h || !in || !out) return set_err(h, ODWF_EINVAL, "null argument");
+    if (!h->have_gauge) return set_err(h, ODWF_EINVAL, "odwf_set_gauge has not been called");
+    if (op != ODWF_OP_DT && op != ODWF_OP_HT && op != ODWF_OP_DODWF) return set_err(h, ODWF_EINVAL, "bad op");
+    if (prec != ODWF_PREC_DOUBLE && prec != ODWF_PREC_SINGLE) return set_err(h, ODWF_EINVAL, "apply: prec must be DOUBLE or SINGLE");
+    int rc;
+    if ((rc = check_mass(h, m1)) || (rc = check_mass(h, m2))) return rc;
+    const int stg = prec == ODWF_PREC_DOUBLE ? ST_DOUBLE : ST_FLOAT;
+    if ((rc = ensure_workspace(h, ST_DOUBLE))) return rc;
+    const SCoef* c = get_coef(h, m1, m2);
+    if (!c) return ODWF_EINVAL;
+    Workspace& w = h->ws;
+    void *ie = w.b_e, *io = w.b_o, *oe = w.x_e, *oo = w.x_o;
+    if (op == ODWF_OP_DODWF) return set_err(h, ODWF_EINVAL, "D_odwf apply is provided by apply_dodwf");
+    // H_T = g5 R5 D_T ; H_T^dag = H_T. D_T^dag = g5 (D_T with transposed M) g5.
+    // For H_T: out = g5 R5 D_T in  -> pack in plainly, unpack with R5 g5.
+    // For H_T^dag = D_T^dag R5 g5: pack with R5 g5, apply D_T^dag, unpack plainly.
+    const bool ht = (op == ODWF_OP_HT);
+    const int pack_flag = (ht && dag) ? 1 : 0;
+    const int unpack_flag = (ht && !dag) ? 1 : 0;
+    if ((rc = launch_pack5(h, (const double*)in, ie, io, stg, pack_flag, st))) return rc;
+    if ((rc = apply_dt_parity(h, stg, c, dag, 0, io, ie, oe, st))) return rc;
+    if ((rc = apply_dt_parity(h, stg, c, dag, 1, ie, io, oo, st))) return rc;
+    return launch_unpack5(h, oe, oo, (double*)out, stg, unpack_flag, st);
+}
+
+}  // namespace odwf
+
+extern "C" {
+
+int odwf_apply(odwf_t* h, int op, double m1, double m2, const void* in, void* out, int prec, void* stream) {
+    return odwf::apply_common(h, op, m1, m2, in, out, prec, false, (cudaStream_t)stream);
+}
+
+int odwf_apply_dag(odwf_t* h, int op, double m1, double m2, const void* in, void* out, int prec, void* stream) {
+    return odwf::apply_common(h, op, m1, m2, in, out, prec, true, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+// ---- kernel timing -----------------------------------------------------------------------------
+namespace odwf {
+
+static cudaEvent_t prof_event(odwf_s* h) {
+    if (!h->prof_pool.empty()) {
+        cudaEvent_t e = h->prof_pool.back();
+        h->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_begin(odwf_s* h, int, cudaStream_t st, cudaEvent_t* a) {
+    *a = prof_event(h);
+    cudaEventRecord(*a, st);
+}
+
+void prof_end(odwf_s* h, int key, cudaStream_t st, cudaEvent_t a) {
+    cudaEvent_t b = prof_event(h);
+    cudaEventRecord(b, st);
+    h->prof_recs.push_back({key, a, b});
+}
+
+}  // namespace odwf
+
+extern "C" int odwf_profile_enable(odwf_t* h, int enable) {
+    if (!h) return ODWF_EINVAL;
+    for (auto& r : h->prof_recs) {
+        h->prof_pool.push_back(r.a);
+        h->prof_pool.push_back(r.b);
+    }
+    h->prof_recs.clear();
+    h->prof = enable != 0;
+    return ODWF_OK;
+}
+
+extern "C" int odwf_profile_read(odwf_t* h, int* keys, int* launches, double* total_ms, int* n_io) {
+    if (!h || !n_io) return ODWF_EINVAL;
+    int rc = cuda_check(h, cudaDeviceSynchronize(), "profile sync");
+    if (rc) return rc;
+    std::map<int, std::pair<int, double>> acc;
+    for (auto& r : h->prof_recs) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        auto& e = acc[r.key];
+        e.first += 1;
+        e.second += ms;
+    }
+    int i = 0;
+    for (auto& kv : acc) {
+        if (i < *n_io && keys && launches && total_ms) {
+            keys[i] = kv.first;
+            launches[i] = kv.second.first;
+            total_ms[i] = kv.second.second;
+        }
+        ++i;
+    }
+    *n_io = i;
+    return ODWF_OK;
+}

@@ -1,0 +1,690 @@
+// Hopping (dslash) kernels of D_T(m1, m2) and the even-odd Schur complement, plus layout and
+// BLAS-1 kernels.
+//
+// Operator (Eq.(DTm1m2), read with c = 1, d = 0):
+//   D_T(m1, m2) = D_w(-m0) + P_+ M_+(m1) + P_- M_-(m2),
+//   D_w(-m0)    = (4 - m0) - 1/2 H,
+//   H psi(x)    = sum_mu (1 - gamma_mu) U_mu(x) psi(x+mu) + (1 + gamma_mu) U_mu^dag(x-mu) psi(x-mu).
+// The hop H is diagonal in s, so one gauge link serves all Ns slices of a site. Each CTA owns all
+// Ns slices of `spb` checkerboard sites (threadIdx.x = s, threadIdx.y = site), which lets the
+// fifth-dimension part (a dense Ns x Ns matrix per chirality, applied to the hop sum or to the
+// own-site field) be fused into the same pass through shared memory.
+//
+// Spin projection in the chiral basis gamma_5 = diag(1,1,-1,-1), gamma_mu = [[0, B_mu],[C_mu, 0]]
+// with C_mu = B_mu^dag unitary: (1 -/+ gamma_mu) psi = [h; -/+ C h], h = psi_up -/+ B psi_dn, so each
+// direction multiplies one 2-spin half spinor by U.
+#include <cstdio>
+
+#include "field_access.cuh"
+
+namespace odwf {
+
+// ---- complex helpers on interleaved real arrays ------------------------------------------------
+// spinor index of (spin, color) real part: (spin * 3 + color) * 2
+
+template <typename R>
+__device__ __forceinline__ void cadd(R* o, const R* a) { o[0] += a[0]; o[1] += a[1]; }
+
+// h = psi_up + SIGN * B_mu psi_dn  (SIGN = -1 for 1 - gamma_mu, +1 for 1 + gamma_mu)
+template <int MU, int SIGN, typename R>
+__device__ __forceinline__ void project(const R* p, R* h) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const R* u0 = p + (0 * 3 + c) * 2;
+        const R* u1 = p + (1 * 3 + c) * 2;
+        const R* d0 = p + (2 * 3 + c) * 2;
+        const R* d1 = p + (3 * 3 + c) * 2;
+        R* h0 = h + (0 * 3 + c) * 2;
+        R* h1 = h + (1 * 3 + c) * 2;
+        if (MU == 0) {  // B = -i sigma_1: (B d)_0 = -i d1, (B d)_1 = -i d0; -i z = (z.im, -z.re)
+            h0[0] = u0[0] + SIGN * d1[1]; h0[1] = u0[1] - SIGN * d1[0];
+            h1[0] = u1[0] + SIGN * d0[1]; h1[1] = u1[1] - SIGN * d0[0];
+        } else if (MU == 1) {  // B = -i sigma_2 = [[0,-1],[1,0]]: (B d)_0 = -d1, (B d)_1 = d0
+            h0[0] = u0[0] - SIGN * d1[0]; h0[1] = u0[1] - SIGN * d1[1];
+            h1[0] = u1[0] + SIGN * d0[0]; h1[1] = u1[1] + SIGN * d0[1];
+        } else if (MU == 2) {  // B = -i sigma_3: (B d)_0 = -i d0, (B d)_1 = +i d1; i z = (-z.im, z.re)
+            h0[0] = u0[0] + SIGN * d0[1]; h0[1] = u0[1] - SIGN * d0[0];
+            h1[0] = u1[0] - SIGN * d1[1]; h1[1] = u1[1] + SIGN * d1[0];
+        } else {  // B = 1
+            h0[0] = u0[0] + SIGN * d0[0]; h0[1] = u0[1] + SIGN * d0[1];
+            h1[0] = u1[0] + SIGN * d1[0]; h1[1] = u1[1] + SIGN * d1[1];
+        }
+    }
+}
+
+// v_up += w ; v_dn += SIGN * C_mu w   (SIGN = -1 for 1 - gamma_mu, +1 for 1 + gamma_mu)
+template <int MU, int SIGN, typename R>
+__device__ __forceinline__ void reconstruct(R* v, const R* w) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const R* w0 = w + (0 * 3 + c) * 2;
+        const R* w1 = w + (1 * 3 + c) * 2;
+        R* v0 = v + (0 * 3 + c) * 2;
+        R* v1 = v + (1 * 3 + c) * 2;
+        R* v2 = v + (2 * 3 + c) * 2;
+        R* v3 = v + (3 * 3 + c) * 2;
+        cadd(v0, w0);
+        cadd(v1, w1);
+        if (MU == 0) {  // C = i sigma_1: (C w)_0 = i w1, (C w)_1 = i w0
+            v2[0] += SIGN * (-w1[1]); v2[1] += SIGN * w1[0];
+            v3[0] += SIGN * (-w0[1]); v3[1] += SIGN * w0[0];
+        } else if (MU == 1) {  // C = i sigma_2 = [[0,1],[-1,0]]: (C w)_0 = w1, (C w)_1 = -w0
+            v2[0] += SIGN * w1[0]; v2[1] += SIGN * w1[1];
+            v3[0] -= SIGN * w0[0]; v3[1] -= SIGN * w0[1];
+        } else if (MU == 2) {  // C = i sigma_3: (C w)_0 = i w0, (C w)_1 = -i w1
+            v2[0] += SIGN * (-w0[1]); v2[1] += SIGN * w0[0];
+            v3[0] += SIGN * w1[1]; v3[1] += SIGN * (-w1[0]);
+        } else {  // C = 1
+            v2[0] += SIGN * w0[0]; v2[1] += SIGN * w0[1];
+            v3[0] += SIGN * w1[0]; v3[1] += SIGN * w1[1];
+        }
+    }
+}
+
+// w[spin a] = U h[spin a] for the two spins of a half spinor
+template <typename R>
+__device__ __forceinline__ void su3_mul_half(const R* u, const R* h, R* w) {
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            R re = 0, im = 0;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const R ur = u[(i * 3 + j) * 2], ui = u[(i * 3 + j) * 2 + 1];
+                const R hr = h[(a * 3 + j) * 2], hi = h[(a * 3 + j) * 2 + 1];
+                re = fma(ur, hr, re);
+                re = fma(-ui, hi, re);
+                im = fma(ur, hi, im);
+                im = fma(ui, hr, im);
+            }
+            w[(a * 3 + i) * 2] = re;
+            w[(a * 3 + i) * 2 + 1] = im;
+        }
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void g5_flip(R* v) {
+#pragma unroll
+    for (int k = 12; k < 24; ++k) v[k] = -v[k];
+}
+
+template <int ST, int MU>
+__device__ __forceinline__ void hop_dir(const HopArgs& a, const int* n, int cb, int s,
+                                        typename Store<ST>::R* v, bool g5in) {
+    using R = typename Store<ST>::R;
+    R psi[24], h[12], w[12], u[18];
+    // forward: (1 - gamma_mu) U_mu(x) psi(x + mu)
+    Store<ST>::load(a.in, a.in_scale, (size_t)n[MU], s, a.Ns, psi);
+    if (g5in) g5_flip(psi);
+    project<MU, -1>(psi, h);
+    Links<ST>::load(a.links, cb, MU, u);
+    su3_mul_half(u, h, w);
+    reconstruct<MU, -1>(v, w);
+    // backward: (1 + gamma_mu) U_mu(x - mu)^dag psi(x - mu); the stored link is already daggered
+    Store<ST>::load(a.in, a.in_scale, (size_t)n[4 + MU], s, a.Ns, psi);
+    if (g5in) g5_flip(psi);
+    project<MU, +1>(psi, h);
+    Links<ST>::load(a.links, cb, 4 + MU, u);
+    su3_mul_half(u, h, w);
+    reconstruct<MU, +1>(v, w);
+}
+
+// out_k = sum_{s'} M_c[s][s'] w_{s'}k with c = P_+ for k < 12, P_- for k >= 12 (mt transposed)
+template <typename R>
+__device__ __forceinline__ void s_mix(const R* mt, const R* sh_site, int s, int Ns, R* out, bool accumulate) {
+    R acc[24];
+#pragma unroll
+    for (int k = 0; k < 24; ++k) acc[k] = 0;
+    const int NN = Ns * Ns;
+    for (int sp = 0; sp < Ns; ++sp) {
+        const R cp = mt[sp * Ns + s];
+        const R cm = mt[NN + sp * Ns + s];
+        const R* w = sh_site + sp * 24;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[k] = fma(cp, w[k], acc[k]);
+#pragma unroll
+        for (int k = 12; k < 24; ++k) acc[k] = fma(cm, w[k], acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 24; ++k) out[k] = accumulate ? out[k] + acc[k] : acc[k];
+}
+
+__device__ __forceinline__ double block_reduce_sum(double v, double* wsum) {
+    const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
+    const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (blockDim.x * blockDim.y + 31) >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    __syncthreads();
+    if (lane == 0) wsum[warp] = v;
+    __syncthreads();
+    double tot = 0.0;
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        for (int w = 0; w < nwarps; ++w) tot += wsum[w];
+    return tot;  // valid in thread (0,0)
+}
+
+// Deterministic grid reduction: every block writes its partial; the last block to finish sums
+// the partials in index order and runs the epilogue's scalar update.
+template <int EPI>
+__device__ void grid_finalize(const HopArgs& a, double part) {
+    __shared__ double wsum[32];
+    __shared__ int is_last;
+    const double bsum = block_reduce_sum(part, wsum);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        a.partials[blockIdx.x] = bsum;
+        __threadfence();
+        const unsigned t = atomicAdd(&a.state->ticket, 1u);
+        is_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nth = blockDim.x * blockDim.y;
+    double acc = 0.0;
+    for (int i = tid; i < (int)gridDim.x; i += nth) acc += ((volatile double*)a.partials)[i];
+    const double tot = block_reduce_sum(acc, wsum);
+    if (tid == 0) {
+        CGState* st = a.state;
+        st->ticket = 0;
+        if (EPI == EPI_CG_A) {
+            const double rr_new = tot;
+            st->iter += 1;
+            if (!isfinite(rr_new)) {
+                st->flag = FLAG_BREAKDOWN;
+            } else {
+                st->beta = rr_new / st->rr;
+                st->rr = rr_new;
+                if (rr_new > st->rr_max) st->rr_max = rr_new;
+                if (rr_new <= st->tol2) st->flag = FLAG_CONVERGED;
+                else if (st->delta2 > 0.0 && rr_new < st->delta2 * st->rr_max) st->flag = FLAG_UPDATE;
+                else if (st->iter >= st->maxiter) st->flag = FLAG_MAXITER;
+            }
+        } else if (EPI == EPI_CG_B) {
+            st->pp = tot;
+            if (!(tot > 0.0) || !isfinite(tot)) st->flag = FLAG_BREAKDOWN;
+            else st->alpha = st->rr / tot;
+        } else {
+            st->result[a.slot] = tot;
+        }
+    }
+}
+
+// Generic kernel for one output parity:
+//   v = c_hop * H(in)                              (HOP; in gets gamma_5 if G5_HOP_IN)
+//   v += a_own * own                               (OWN && !MIXOWN; own gets gamma_5 if G5_OWN_IN)
+//   v = Mhop v                                     (MIXHOP)
+//   v += Mown own                                  (MIXOWN)
+//   v = gamma_5 v                                  (G5_OUT)
+//   epilogue EPI
+template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
+__global__ void __launch_bounds__(256) k_hop(HopArgs a) {
+    using S = Store<ST>;
+    using R = typename S::R;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Ns = a.Ns;
+    const int s = threadIdx.x, ls = threadIdx.y, spb = blockDim.y;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+    R* mh = reinterpret_cast<R*>(smem_raw);
+    R* mo = mh + (MIXHOP ? 2 * Ns * Ns : 0);
+    R* sh = mo + (MIXOWN ? 2 * Ns * Ns : 0);
+    constexpr bool REDUCE = (EPI != EPI_STORE);
+
+    if (a.state != nullptr && EPI != EPI_STORE_NORM && EPI != EPI_RESID) {
+        if (((volatile CGState*)a.state)->flag != FLAG_RUN) return;
+    }
+    for (int i = tid; i < 2 * Ns * Ns; i += nth) {
+        if (MIXHOP) mh[i] = (R)a.mhop[i];
+        if (MIXOWN) mo[i] = (R)a.mown[i];
+    }
+    double alpha = 0.0, beta = 0.0;
+    if (EPI == EPI_CG_A) alpha = a.state->alpha;
+    if (EPI == EPI_CG_B) beta = a.state->beta;
+    const bool g5h = (a.g5 & G5_HOP_IN) != 0, g5o = (a.g5 & G5_OWN_IN) != 0, g5out = (a.g5 & G5_OUT) != 0;
+    const R chop = (R)a.c_hop, aown = (R)a.a_own;
+    double part = 0.0;
+
+    for (int g = blockIdx.x; g * spb < a.Vh; g += gridDim.x) {
+        __syncthreads();
+        const int cb = g * spb + ls;
+        const bool valid = cb < a.Vh;
+        R v[24];
+#pragma unroll
+        for (int k = 0; k < 24; ++k) v[k] = 0;
+        if (HOP && valid) {
+            int n[8];
+            const int4* nb = reinterpret_cast<const int4*>(a.nbr + (size_t)cb * 8);
+            int4 n0 = __ldg(nb), n1 = __ldg(nb + 1);
+            n[0] = n0.x; n[1] = n0.y; n[2] = n0.z; n[3] = n0.w;
+            n[4] = n1.x; n[5] = n1.y; n[6] = n1.z; n[7] = n1.w;
+            hop_dir<ST, 0>(a, n, cb, s, v, g5h);
+            hop_dir<ST, 1>(a, n, cb, s, v, g5h);
+            hop_dir<ST, 2>(a, n, cb, s, v, g5h);
+            hop_dir<ST, 3>(a, n, cb, s, v, g5h);
+#pragma unroll
+            for (int k = 0; k < 24; ++k) v[k] *= chop;
+        }
+        R ow[24];
+        if (OWN) {
+            if (valid) {
+                S::load(a.own, a.own_scale, (size_t)cb, s, Ns, ow);
+                if (g5o) g5_flip(ow);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 24; ++k) ow[k] = 0;
+            }
+            if (!MIXOWN) {
+#pragma unroll
+                for (int k = 0; k < 24; ++k) v[k] = fma(aown, ow[k], v[k]);
+            }
+        }
+        if (MIXHOP) {
+            R* dst = sh + (ls * Ns + s) * 24;
+#pragma unroll
+            for (int k = 0; k < 24; ++k) dst[k] = v[k];
+            __syncthreads();
+            s_mix(mh, sh + ls * Ns * 24, s, Ns, v, false);
+        }
+        if (MIXOWN) {
+            if (MIXHOP) __syncthreads();
+            R* dst = sh + (ls * Ns + s) * 24;
+#pragma unroll
+            for (int k = 0; k < 24; ++k) dst[k] = ow[k];
+            __syncthreads();
+            s_mix(mo, sh + ls * Ns * 24, s, Ns, v, true);
+        }
+        if (g5out) g5_flip(v);
+        if (!valid) continue;
+
+        if (EPI == EPI_STORE || EPI == EPI_STORE_NORM) {
+            S::store(a.out, a.out_scale, (size_t)cb, s, Ns, v);
+            if (EPI == EPI_STORE_NORM) {
+                R t = 0;
+#pragma unroll
+                for (int k = 0; k < 24; ++k) t = fma(v[k], v[k], t);
+                part += (double)t;
+            }
+        } else if (EPI == EPI_RESID) {
+            R b[24];
+            S::load(a.x, a.x_scale, (size_t)cb, s, Ns, b);
+            R t = 0;
+#pragma unroll
+            for (int k = 0; k < 24; ++k) {
+                b[k] -= v[k];
+                t = fma(b[k], b[k], t);
+            }
+            S::store(a.out, a.out_scale, (size_t)cb, s, Ns, b);
+            part += (double)t;
+        } else if (EPI == EPI_CG_A) {
+            // x += alpha * own (own = p, without gamma_5), r -= alpha * v
+            R x[24], r[24];
+            S::load(a.x, a.x_scale, (size_t)cb, s, Ns, x);
+            S::load(a.r, a.r_scale, (size_t)cb, s, Ns, r);
+            const R al = (R)alpha;
+            R t = 0;
+#pragma unroll
+            for (int k = 0; k < 24; ++k) {
+                x[k] = fma(al, ow[k], x[k]);
+                r[k] = fma(-al, v[k], r[k]);
+                t = fma(r[k], r[k], t);
+            }
+            S::store(a.x, a.x_scale, (size_t)cb, s, Ns, x);
+            S::store(a.r, a.r_scale, (size_t)cb, s, Ns, r);
+            part += (double)t;
+        } else if (EPI == EPI_CG_B) {
+            // p = v + beta * p
+            R p[24];
+            S::load(a.r, a.r_scale, (size_t)cb, s, Ns, p);
+            const R be = (R)beta;
+            R t = 0;
+#pragma unroll
+            for (int k = 0; k < 24; ++k) {
+                p[k] = fma(be, p[k], v[k]);
+                t = fma(p[k], p[k], t);
+            }
+            S::store(a.r, a.r_scale, (size_t)cb, s, Ns, p);
+            part += (double)t;
+        }
+    }
+    if (REDUCE) grid_finalize<EPI>(a, part);
+}
+
+// ---- launch ------------------------------------------------------------------------------------
+// Sites per CTA: the CTA holds spb * Ns threads, a multiple of 32 and at least 128.
+int spb_for(int Ns) {
+    int g = 32, n = Ns;
+    while (n) { int t = g % n; g = n; n = t; }  // gcd(32, Ns)
+    const int base = 32 / g;
+    int spb = base;
+    while (spb * Ns < 128) spb += base;
+    return spb;
+}
+
+template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
+static int launch_one(odwf_s* h, int parity, HopArgs a, cudaStream_t st) {
+    using R = typename Store<ST>::R;
+    auto fn = k_hop<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>;
+    const int Ns = h->Ns, spb = spb_for(Ns);
+    const size_t smem = sizeof(R) * ((size_t)(MIXHOP + MIXOWN) * 2 * Ns * Ns + (size_t)spb * Ns * 24);
+    static int occ_cache[kMaxNs + 1] = {0};
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        attr_set = true;
+    }
+    int& occ = occ_cache[Ns];
+    if (occ == 0) {
+        int o = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, Ns * spb, smem) != cudaSuccess || o < 1) o = 1;
+        occ = o;
+    }
+    const int groups = (h->Vh + spb - 1) / spb;
+    int grid = h->num_sms * occ;
+    if (grid > groups) grid = groups;
+    if (grid < 1) grid = 1;
+    if (EPI != EPI_STORE && grid > h->partials_n) return set_err(h, ODWF_EINVAL, "partials buffer too small");
+    a.links = (ST == ST_DOUBLE) ? (const void*)h->U64[parity] : (const void*)h->U32[parity];
+    a.nbr = h->nbr[parity];
+    a.Vh = h->Vh;
+    a.Ns = Ns;
+    a.partials = h->partials;
+    if (EPI != EPI_STORE && a.state == nullptr) a.state = h->state;
+    const int key = ST * 100000 + HOP * 10000 + MIXHOP * 1000 + OWN * 100 + MIXOWN * 10 + EPI;
+    cudaEvent_t ev0 = nullptr;
+    if (h->prof) prof_begin(h, key, st, &ev0);
+    fn<<<grid, dim3(Ns, spb), smem, st>>>(a);
+    if (h->prof) prof_end(h, key, st, ev0);
+    return cuda_check(h, cudaGetLastError(), "k_hop launch");
+}
+
+template <int ST>
+static int launch_st(odwf_s* h, int parity, bool hop, bool mixhop, bool own, bool mixown, int epi, HopArgs a,
+                     cudaStream_t st) {
+#define ODWF_CASE(HOPV, MH, OW, MO, E)                                                          \
+    if (hop == HOPV && mixhop == MH && own == OW && mixown == MO && epi == E)                     \
+        return launch_one<ST, HOPV, MH, OW, MO, E>(h, parity, a, st);
+    ODWF_CASE(true, true, false, false, EPI_STORE)      // K1: t = Mhop c H in
+    ODWF_CASE(true, true, true, false, EPI_STORE)       // t = Mhop (c H in + a own)
+    ODWF_CASE(true, false, true, true, EPI_STORE)       // out = Mown own + c H in
+    ODWF_CASE(true, false, true, true, EPI_STORE_NORM)  // same, |out|^2
+    ODWF_CASE(true, false, true, true, EPI_RESID)       // out = b - (Mown own + c H in)
+    ODWF_CASE(true, false, true, true, EPI_CG_A)        // CGNE forward half step
+    ODWF_CASE(true, false, true, true, EPI_CG_B)        // CGNE adjoint half step
+    ODWF_CASE(true, false, true, false, EPI_STORE)      // out = a own + c H in
+    ODWF_CASE(false, false, true, true, EPI_STORE)      // out = Mown own (s-local)
+#undef ODWF_CASE
+    return set_err(h, ODWF_EINVAL, "unsupported hop kernel variant");
+}
+
+int launch_hop(odwf_s* h, int storage, int parity, bool mixhop, bool own, bool mixown, int epi, HopArgs a,
+               cudaStream_t st) {
+    switch (storage) {
+        case ST_DOUBLE: return launch_st<ST_DOUBLE>(h, parity, true, mixhop, own, mixown, epi, a, st);
+        case ST_FLOAT: return launch_st<ST_FLOAT>(h, parity, true, mixhop, own, mixown, epi, a, st);
+        case ST_HALF: return launch_st<ST_HALF>(h, parity, true, mixhop, own, mixown, epi, a, st);
+    }
+    return set_err(h, ODWF_EINVAL, "bad storage");
+}
+
+int launch_smix(odwf_s* h, int storage, const void* in, void* out, const double* mt, double, cudaStream_t st) {
+    HopArgs a{};
+    a.own = in;
+    a.out = out;
+    a.mown = mt;
+    switch (storage) {
+        case ST_DOUBLE: return launch_st<ST_DOUBLE>(h, 0, false, false, true, true, EPI_STORE, a, st);
+        case ST_FLOAT: return launch_st<ST_FLOAT>(h, 0, false, false, true, true, EPI_STORE, a, st);
+    }
+    return set_err(h, ODWF_EINVAL, "bad storage for smix");
+}
+
+// ---- layout kernels ----------------------------------------------------------------------------
+// ABI 5D lexicographic complex128 [s][lex][12] <-> internal even-odd chunked storage.
+template <int ST>
+__global__ void k_pack5(const double2* __restrict__ lex5, void* e, void* o, float* es, float* os,
+                        const int* __restrict__ lex_e, const int* __restrict__ lex_o, int Vh, int V, int Ns,
+                        int r5g5) {
+    using R = typename Store<ST>::R;
+    const size_t total = (size_t)2 * Vh * Ns;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int s = (int)(i % Ns);
+        const size_t rest = i / Ns;
+        const int cb = (int)(rest % Vh);
+        const int par = (int)(rest / Vh);
+        const int lex = par ? lex_o[cb] : lex_e[cb];
+        const int sin = r5g5 ? (Ns - 1 - s) : s;
+        const double2* src = lex5 + ((size_t)sin * V + lex) * 12;
+        R v[24];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            double2 c = src[k];
+            const double sg = (r5g5 && k >= 6) ? -1.0 : 1.0;
+            v[2 * k] = (R)(sg * c.x);
+            v[2 * k + 1] = (R)(sg * c.y);
+        }
+        Store<ST>::store(par ? o : e, par ? os : es, cb, s, Ns, v);
+    }
+}
+
+template <int ST>
+__global__ void k_unpack5(const void* e, const void* o, const float* es, const float* os, double2* __restrict__ lex5,
+                          const int* __restrict__ lex_e, const int* __restrict__ lex_o, int Vh, int V, int Ns,
+                          int r5g5) {
+    using R = typename Store<ST>::R;
+    const size_t total = (size_t)2 * Vh * Ns;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int s = (int)(i % Ns);
+        const size_t rest = i / Ns;
+        const int cb = (int)(rest % Vh);
+        const int par = (int)(rest / Vh);
+        const int lex = par ? lex_o[cb] : lex_e[cb];
+        R v[24];
+        Store<ST>::load(par ? o : e, par ? os : es, cb, s, Ns, v);
+        const int sout = r5g5 ? (Ns - 1 - s) : s;
+        double2* dst = lex5 + ((size_t)sout * V + lex) * 12;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const double sg = (r5g5 && k >= 6) ? -1.0 : 1.0;
+            dst[k] = make_double2(sg * (double)v[2 * k], sg * (double)v[2 * k + 1]);
+        }
+    }
+}
+
+static int grid_1d(odwf_s* h, size_t n) {
+    size_t g = (n + 255) / 256;
+    const size_t cap = (size_t)h->num_sms * 16;
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+int launch_pack5(odwf_s* h, const double* lex5, void* e, void* o, int storage, int r5g5, cudaStream_t st) {
+    const size_t n = (size_t)2 * h->Vh * h->Ns;
+    const int g = grid_1d(h, n);
+    if (storage == ST_DOUBLE)
+        k_pack5<ST_DOUBLE><<<g, 256, 0, st>>>((const double2*)lex5, e, o, nullptr, nullptr, h->lexof[0], h->lexof[1],
+                                              h->Vh, h->V, h->Ns, r5g5);
+    else if (storage == ST_FLOAT)
+        k_pack5<ST_FLOAT><<<g, 256, 0, st>>>((const double2*)lex5, e, o, nullptr, nullptr, h->lexof[0], h->lexof[1],
+                                             h->Vh, h->V, h->Ns, r5g5);
+    else
+        return set_err(h, ODWF_EINVAL, "pack5: storage");
+    return cuda_check(h, cudaGetLastError(), "k_pack5");
+}
+
+int launch_unpack5(odwf_s* h, const void* e, const void* o, double* lex5, int storage, int r5g5, cudaStream_t st) {
+    const size_t n = (size_t)2 * h->Vh * h->Ns;
+    const int g = grid_1d(h, n);
+    if (storage == ST_DOUBLE)
+        k_unpack5<ST_DOUBLE><<<g, 256, 0, st>>>(e, o, nullptr, nullptr, (double2*)lex5, h->lexof[0], h->lexof[1],
+                                                h->Vh, h->V, h->Ns, r5g5);
+    else if (storage == ST_FLOAT)
+        k_unpack5<ST_FLOAT><<<g, 256, 0, st>>>(e, o, nullptr, nullptr, (double2*)lex5, h->lexof[0], h->lexof[1],
+                                               h->Vh, h->V, h->Ns, r5g5);
+    else
+        return set_err(h, ODWF_EINVAL, "unpack5: storage");
+    return cuda_check(h, cudaGetLastError(), "k_unpack5");
+}
+
+// ---- elementwise kernels over one half field (Vh * Ns spinors) ---------------------------------
+template <int STI, int STO>
+__global__ void k_convert(const void* in, const float* isc, void* out, float* osc, int Vh, int Ns) {
+    using RI = typename Store<STI>::R;
+    using RO = typename Store<STO>::R;
+    const size_t total = (size_t)Vh * Ns;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int s = (int)(i % Ns);
+        const size_t cb = i / Ns;
+        RI v[24];
+        RO w[24];
+        Store<STI>::load(in, isc, cb, s, Ns, v);
+#pragma unroll
+        for (int k = 0; k < 24; ++k) w[k] = (RO)v[k];
+        Store<STO>::store(out, osc, cb, s, Ns, w);
+    }
+}
+
+template <int STI>
+__global__ void k_axpy_to64(double a, const void* x, const float* xsc, double* y, int Vh, int Ns) {
+    using RI = typename Store<STI>::R;
+    const size_t total = (size_t)Vh * Ns;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int s = (int)(i % Ns);
+        const size_t cb = i / Ns;
+        RI v[24];
+        double w[24];
+        Store<STI>::load(x, xsc, cb, s, Ns, v);
+        Store<ST_DOUBLE>::load(y, nullptr, cb, s, Ns, w);
+#pragma unroll
+        for (int k = 0; k < 24; ++k) w[k] = fma(a, (double)v[k], w[k]);
+        Store<ST_DOUBLE>::store(y, nullptr, cb, s, Ns, w);
+    }
+}
+
+template <int ST>
+__global__ void k_norm2(const void* v, const float* sc, CGState* state, double* partials, int slot, int Vh, int Ns) {
+    using R = typename Store<ST>::R;
+    const size_t total = (size_t)Vh * Ns;
+    double part = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int s = (int)(i % Ns);
+        const size_t cb = i / Ns;
+        R w[24];
+        Store<ST>::load(v, sc, cb, s, Ns, w);
+        double t = 0.0;
+#pragma unroll
+        for (int k = 0; k < 24; ++k) t += (double)w[k] * (double)w[k];
+        part += t;
+    }
+    HopArgs a{};
+    a.state = state;
+    a.partials = partials;
+    a.slot = slot;
+    grid_finalize<EPI_STORE_NORM>(a, part);
+}
+
+static int convert_dispatch(odwf_s* h, const void* in, int sti, const float* isc, void* out, int sto, float* osc,
+                            cudaStream_t st) {
+    const int g = grid_1d(h, (size_t)h->Vh * h->Ns);
+#define ODWF_CV(A, B)                                                                              \
+    if (sti == A && sto == B) {                                                                    \
+        k_convert<A, B><<<g, 256, 0, st>>>(in, isc, out, osc, h->Vh, h->Ns);                       \
+        return cuda_check(h, cudaGetLastError(), "k_convert");                                     \
+    }
+    ODWF_CV(ST_DOUBLE, ST_FLOAT)
+    ODWF_CV(ST_DOUBLE, ST_HALF)
+    ODWF_CV(ST_FLOAT, ST_DOUBLE)
+    ODWF_CV(ST_HALF, ST_DOUBLE)
+    ODWF_CV(ST_DOUBLE, ST_DOUBLE)
+    ODWF_CV(ST_FLOAT, ST_FLOAT)
+#undef ODWF_CV
+    return set_err(h, ODWF_EINVAL, "convert: unsupported pair");
+}
+
+int launch_convert(odwf_s* h, const void* in, int st_in, const float* in_scale, void* out, int st_out,
+                   float* out_scale, cudaStream_t st) {
+    return convert_dispatch(h, in, st_in, in_scale, out, st_out, out_scale, st);
+}
+
+int launch_axpy_to64(odwf_s* h, double a, const void* x, int st_in, const float* xsc, double* y, cudaStream_t st) {
+    const int g = grid_1d(h, (size_t)h->Vh * h->Ns);
+    if (st_in == ST_FLOAT) k_axpy_to64<ST_FLOAT><<<g, 256, 0, st>>>(a, x, xsc, y, h->Vh, h->Ns);
+    else if (st_in == ST_HALF) k_axpy_to64<ST_HALF><<<g, 256, 0, st>>>(a, x, xsc, y, h->Vh, h->Ns);
+    else k_axpy_to64<ST_DOUBLE><<<g, 256, 0, st>>>(a, x, xsc, y, h->Vh, h->Ns);
+    return cuda_check(h, cudaGetLastError(), "k_axpy_to64");
+}
+
+int launch_norm2(odwf_s* h, const void* v, int storage, const float* sc, int slot, cudaStream_t st) {
+    int g = grid_1d(h, (size_t)h->Vh * h->Ns);
+    if (g > h->partials_n) g = h->partials_n;
+    if (storage == ST_DOUBLE) k_norm2<ST_DOUBLE><<<g, 256, 0, st>>>(v, sc, h->state, h->partials, slot, h->Vh, h->Ns);
+    else if (storage == ST_FLOAT) k_norm2<ST_FLOAT><<<g, 256, 0, st>>>(v, sc, h->state, h->partials, slot, h->Vh, h->Ns);
+    else k_norm2<ST_HALF><<<g, 256, 0, st>>>(v, sc, h->state, h->partials, slot, h->Vh, h->Ns);
+    return cuda_check(h, cudaGetLastError(), "k_norm2");
+}
+
+// ---- gauge field -------------------------------------------------------------------------------
+// U (ABI): [mu][lex][3][3] complex128. Output per parity p and checkerboard site cb:
+//   dir mu     : U_mu(x), times -1 when mu = t and x_t = Lt - 1 (antiperiodic fermion boundary)
+//   dir 4 + mu : U_mu(x - mu)^dag, times -1 when mu = t and x_t = 0
+__global__ void k_gauge(const double2* __restrict__ U, double* __restrict__ U64e, double* __restrict__ U64o,
+                        float* __restrict__ U32e, float* __restrict__ U32o, const int* __restrict__ lex_e,
+                        const int* __restrict__ lex_o, int Lx, int Ly, int Lz, int Lt, int Vh) {
+    const int V = 2 * Vh;
+    const int total = 2 * Vh * 8;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int dir = i % 8;
+        const int rest = i / 8;
+        const int cb = rest % Vh;
+        const int par = rest / Vh;
+        const int lex = par ? lex_o[cb] : lex_e[cb];
+        int c[4];
+        c[0] = lex % Lx;
+        c[1] = (lex / Lx) % Ly;
+        c[2] = (lex / (Lx * Ly)) % Lz;
+        c[3] = lex / (Lx * Ly * Lz);
+        const int L[4] = {Lx, Ly, Lz, Lt};
+        const int mu = dir & 3;
+        double m[18];
+        if (dir < 4) {
+            const double sg = (mu == 3 && c[3] == Lt - 1) ? -1.0 : 1.0;
+            const double2* src = U + ((size_t)mu * V + lex) * 9;
+            for (int k = 0; k < 9; ++k) {
+                m[2 * k] = sg * src[k].x;
+                m[2 * k + 1] = sg * src[k].y;
+            }
+        } else {
+            int d[4] = {c[0], c[1], c[2], c[3]};
+            d[mu] = (d[mu] + L[mu] - 1) % L[mu];
+            const int lexn = d[0] + Lx * (d[1] + Ly * (d[2] + Lz * d[3]));
+            const double sg = (mu == 3 && c[3] == 0) ? -1.0 : 1.0;
+            const double2* src = U + ((size_t)mu * V + lexn) * 9;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {  // (U^dag)_{ab} = conj(U_{ba})
+                    m[(a * 3 + b) * 2] = sg * src[b * 3 + a].x;
+                    m[(a * 3 + b) * 2 + 1] = -sg * src[b * 3 + a].y;
+                }
+        }
+        double* d64 = (par ? U64o : U64e) + ((size_t)cb * 8 + dir) * 18;
+        float* d32 = (par ? U32o : U32e) + ((size_t)cb * 8 + dir) * 20;
+        for (int k = 0; k < 18; ++k) {
+            d64[k] = m[k];
+            d32[k] = (float)m[k];
+        }
+        d32[18] = 0.f;
+        d32[19] = 0.f;
+    }
+}
+
+int launch_gauge(odwf_s* h, const double* U, cudaStream_t st) {
+    const int total = 2 * h->Vh * 8;
+    int g = (total + 255) / 256;
+    if (g > h->num_sms * 16) g = h->num_sms * 16;
+    k_gauge<<<g, 256, 0, st>>>((const double2*)U, h->U64[0], h->U64[1], h->U32[0], h->U32[1], h->lexof[0],
+                               h->lexof[1], h->L[0], h->L[1], h->L[2], h->L[3], h->Vh);
+    return cuda_check(h, cudaGetLastError(), "k_gauge");
+}
+
+}  // namespace odwf

@@ -1,0 +1,174 @@
+// Internal declarations of the optimal domain-wall / EOFA library (not part of the ABI).
+//
+// Internal field layout ("even-odd chunked"): a 5D half-lattice field of one parity holds, for
+// every checkerboard site cb (lexicographic index / 2) and slice s, the 12 complex spinor
+// components (spin-major, then color). They are stored as 16-byte chunks,
+//     chunk(cb, j, s) at ((cb * NCH + j) * Ns + s),
+// NCH = 12 (FP64: one complex per chunk), 6 (FP32: two complex per chunk) or 3 (FP16: four
+// complex per chunk, plus one float scale per (cb, s)). The Ns slices of one chunk of one site are
+// contiguous, so the Ns threads of a site read 16*Ns contiguous bytes per chunk.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "odwf.h"
+
+namespace odwf {
+
+constexpr int kMaxNs = 32;
+
+// ---- Krylov solver state in device memory ------------------------------------------------------
+enum : int { FLAG_RUN = 0, FLAG_CONVERGED = 1, FLAG_UPDATE = 2, FLAG_BREAKDOWN = 3, FLAG_MAXITER = 4 };
+
+struct CGState {
+    double rr;        // |r|^2 of the iterated residual
+    double pp;        // |p|^2
+    double alpha, beta;
+    double tol2;      // stop when rr <= tol2
+    double rr_max;    // max rr since the last reliable update
+    double delta2;    // request a reliable update when rr < delta2 * rr_max (0: never)
+    double result[4]; // reductions of the RESID / NORM epilogues
+    int flag;         // FLAG_*; every solver kernel returns at once when flag != 0
+    int iter;
+    int maxiter;
+    unsigned int ticket;
+};
+
+// ---- kernel epilogues --------------------------------------------------------------------------
+enum : int {
+    EPI_STORE = 0,       // out = v
+    EPI_STORE_NORM = 1,  // out = v, result[slot] = |v|^2
+    EPI_CG_A = 2,        // CGNE: x += alpha own, r -= alpha v, rr = |r|^2 (then beta)
+    EPI_CG_B = 3,        // CGNE: p = v + beta p, pp = |p|^2 (then alpha)
+    EPI_RESID = 4,       // out = b - v, result[slot] = |out|^2
+};
+
+// gamma_5 flags of the generic hopping kernel
+enum : int { G5_HOP_IN = 1, G5_OWN_IN = 2, G5_OUT = 4 };
+
+enum StorageKind : int { ST_DOUBLE = 0, ST_FLOAT = 1, ST_HALF = 2 };
+
+// Arguments of the generic 5D hopping kernel (one output parity). Field pointers are to the
+// storage type of the instantiation; links/nbr are those of the output parity.
+struct HopArgs {
+    const void* in;      // hopped field (opposite parity)
+    const void* own;     // field at the output sites (same parity), used by OWN kernels
+    void* out;
+    const void* links;   // [Vh][8][LINK_STRIDE] : 4 forward U_mu(x), 4 backward U_mu(x-mu)^dag
+    const int* nbr;      // [Vh][8] checkerboard index of x+mu (0..3), x-mu (4..7)
+    const double* mhop;  // 2*Ns*Ns, transposed s-matrices (P_+ then P_-) applied to the hop sum
+    const double* mown;  // 2*Ns*Ns, transposed s-matrices applied to the own field
+    const float* in_scale;   // FP16 per-(cb,s) scales of `in`, `own`, `out` (else null)
+    const float* own_scale;
+    float* out_scale;
+    void* x;             // CG_A: solution; RESID: b
+    void* r;             // CG_A: residual; CG_B: search direction p
+    float* x_scale;
+    float* r_scale;
+    CGState* state;      // may be null for plain applies
+    double* partials;    // [gridDim.x] block partial sums
+    double c_hop;        // coefficient of the hop sum
+    double a_own;        // coefficient of `own` added before the hop-mix (OWN && !MIXOWN)
+    int g5;              // G5_* flags
+    int Vh, Ns;
+    int slot;            // result slot of NORM / RESID
+};
+
+// ---- host-side handle --------------------------------------------------------------------------
+struct SCoef {
+    // 8 transposed Ns x Ns matrices, in this order:
+    //  0 A_+(m1), 1 A_-(m2), 2 A_+^{-1}, 3 A_-^{-1}, 4 A_+^T, 5 A_-^T, 6 A_+^{-T}, 7 A_-^{-T}
+    // "transposed" means stored as Mt[s'][s] = M[s][s'] so thread s reads consecutive words.
+    double* dev = nullptr;
+};
+
+struct Workspace {
+    // FP64 half fields
+    void* b_e = nullptr; void* b_o = nullptr;   // b' = R5 g5 b by parity
+    void* x_e = nullptr; void* x_o = nullptr;
+    void* r64 = nullptr; void* t64 = nullptr; void* bh = nullptr;
+    // inner-precision half fields (storage of the inner solver)
+    void* xi = nullptr; void* ri = nullptr; void* pi = nullptr; void* ti = nullptr;
+    float* xi_s = nullptr; float* ri_s = nullptr; float* pi_s = nullptr; float* ti_s = nullptr;
+    size_t inner_bytes = 0;
+};
+
+}  // namespace odwf
+
+struct odwf_s {
+    int L[4] = {0, 0, 0, 0};
+    int V = 0, Vh = 0, Ns = 0;
+    double m0 = 0;
+    std::vector<double> omega;
+    std::string err;
+    int num_sms = 0;
+    // geometry tables, per output parity
+    int* nbr[2] = {nullptr, nullptr};
+    int* lexof[2] = {nullptr, nullptr};   // lexicographic site of (parity, cb)
+    // links, per output parity: FP64 [Vh][8][18], FP32 [Vh][8][20], FP16 [Vh][8][24 halves]
+    double* U64[2] = {nullptr, nullptr};
+    float* U32[2] = {nullptr, nullptr};
+    bool have_gauge = false;
+    std::map<std::pair<double, double>, odwf::SCoef> coefs;
+    // reductions
+    double* partials = nullptr;
+    int partials_n = 0;
+    odwf::CGState* state = nullptr;        // device
+    odwf::CGState* state_host = nullptr;   // pinned mirror
+    odwf::Workspace ws;
+    // scratch full-lattice FP64 fields for apply / EOFA
+    void* f64[4] = {nullptr, nullptr, nullptr, nullptr};
+    // 4D scratch
+    double* acc4 = nullptr;
+    // kernel timing (odwf_profile_*)
+    bool prof = false;
+    struct ProfRec { int key; cudaEvent_t a, b; };
+    std::vector<ProfRec> prof_recs;
+    std::vector<cudaEvent_t> prof_pool;
+};
+
+namespace odwf {
+
+// sizes
+inline size_t half_elems_bytes(const odwf_s* h, int st) {
+    size_t n = (size_t)h->Vh * h->Ns;
+    switch (st) {
+        case ST_DOUBLE: return n * 24 * sizeof(double);
+        case ST_FLOAT: return n * 24 * sizeof(float);
+        default: return n * 24 * sizeof(__half);
+    }
+}
+
+int set_err(odwf_s* h, int code, const std::string& msg);
+int cuda_check(odwf_s* h, cudaError_t e, const char* what);
+const SCoef* get_coef(odwf_s* h, double m1, double m2);
+
+// launch helpers (kernels.cu)
+// Generic hop: out_p = epi( [MIXOWN ? Mown own : 0] + Mhop?( c_hop H in + a_own own ) )
+int launch_hop(odwf_s* h, int storage, int parity, bool mixhop, bool own, bool mixown, int epi,
+               HopArgs a, cudaStream_t st);
+int launch_smix(odwf_s* h, int storage, const void* in, void* out, const double* mt, double scale,
+                cudaStream_t st);
+int launch_pack5(odwf_s* h, const double* lex5, void* e, void* o, int storage, int r5g5, cudaStream_t st);
+int launch_unpack5(odwf_s* h, const void* e, const void* o, double* lex5, int storage, int r5g5,
+                   cudaStream_t st);
+int launch_convert(odwf_s* h, const void* in, int st_in, const float* in_scale, void* out, int st_out,
+                   float* out_scale, cudaStream_t st);
+int launch_axpy_to64(odwf_s* h, double a, const void* xin, int st_in, const float* xin_scale, double* y,
+                     cudaStream_t st);
+int launch_norm2(odwf_s* h, const void* v, int storage, const float* scale, int slot, cudaStream_t st);
+int launch_gauge(odwf_s* h, const double* U, cudaStream_t st);
+int launch_init_state(odwf_s* h, cudaStream_t st);
+void prof_begin(odwf_s* h, int key, cudaStream_t st, cudaEvent_t* a);
+void prof_end(odwf_s* h, int key, cudaStream_t st, cudaEvent_t a);
+
+// field helpers for EOFA (eofa.cu)
+}  // namespace odwf

@@ -1,0 +1,153 @@
+"""GPU parity of the CUDA path against the FP64 CPU oracle, through the C ABI.
+
+Tolerances: FP64 operator applies agree with the oracle to a relative L2 error of 1e-12;
+FP32 applies to 2e-6 (FP32 rounding of ~40 accumulated terms per output component);
+every solve, in every inner precision, must give an FP64 true residual <= 1e-10 when the
+GPU solution is fed into the oracle's H_T.
+"""
+import numpy as np
+import pytest
+
+from oracle import eofa as oeofa
+from oracle import solver as osolver
+from oracle.operators import ODWF as OracleODWF
+from oracle.operators import dt_at_sites
+from paper_1710_09621_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1710_09621_gb300 import build
+    build.build()
+    from paper_1710_09621_gb300 import binding
+    return binding
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+CASES = [
+    # dims, Ns, omega kind, eps, seed : small cases spanning several CTAs, ragged tails (Ns = 8, 6)
+    ((4, 4, 4, 4), 8, "shamir", 0.4, 0),
+    ((6, 2, 2, 2), 8, "zolo", 0.4, 1),
+    ((4, 2, 6, 4), 6, "zolo", 0.4, 2),
+    ((8, 8, 8, 16), 16, "zolo", 0.3, 3),   # more CTA groups than the grid: grid-stride path
+]
+
+
+def _setup(lib, dims, Ns, kind, eps, seed):
+    om = inputs.omega_shamir(Ns) if kind == "shamir" else inputs.omega_zolotarev(Ns, 0.05, 6.2)
+    U = inputs.random_su3_links(dims, eps, seed)
+    lat = lib.ODWF(dims, Ns, 1.3, om)
+    lat.set_gauge(torch.from_numpy(U).cuda())
+    return lat, OracleODWF(U, 1.3, om), U, om
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("m12", [(0.05, 1.0), (0.01, 0.01), (1.0, 0.1)])
+def test_apply_dt_parity(lib, case, m12):
+    lat, op, U, om = _setup(lib, *case)
+    psi = inputs.gaussian_spinor5(case[0], case[1], 100 + case[4])
+    x = torch.from_numpy(psi).cuda()
+    ref = op.dt(psi, *m12)
+    got = lat.apply(x, *m12, op="dt").cpu().numpy()
+    assert _rel(got, ref) < 1e-12
+    got32 = lat.apply(x, *m12, op="dt", prec="single").cpu().numpy()
+    assert _rel(got32, ref) < 2e-6
+    refd = op.dt_dag(psi, *m12)
+    gotd = lat.apply(x, *m12, op="dt", dag=True).cpu().numpy()
+    assert _rel(gotd, refd) < 1e-12
+    refh = op.ht(psi, *m12)
+    goth = lat.apply(x, *m12, op="ht").cpu().numpy()
+    assert _rel(goth, refh) < 1e-12
+    gothd = lat.apply(x, *m12, op="ht", dag=True).cpu().numpy()
+    assert _rel(gothd, refh) < 1e-12  # H_T is Hermitian
+
+
+@pytest.mark.parametrize("case", CASES[:3])
+@pytest.mark.parametrize("prec", ["double", "single", "half"])
+def test_solve_true_residual(lib, case, prec):
+    lat, op, U, om = _setup(lib, *case)
+    b = inputs.gaussian_spinor5(case[0], case[1], 200 + case[4])
+    m1, m2 = 0.05, 0.1
+    x, st = lat.solve(torch.from_numpy(b).cuda(), m1, m2, opts=lib.solve_opts(tol=1e-10, prec=prec))
+    xr = x.cpu().numpy()
+    res = np.linalg.norm(b - op.ht(xr, m1, m2)) / np.linalg.norm(b)
+    assert st["true_residual"] <= 1e-10
+    assert res <= 1.05e-10, res
+    # agrees with the oracle's own solve within condition-number slack
+    xo, info = osolver.solve_ht(op, b, m1, m2, tol=1e-12)
+    assert _rel(xr, xo) < 1e-7
+
+
+def test_solve_zero_rhs_and_errors(lib):
+    lat, op, U, om = _setup(lib, *CASES[0])
+    z = torch.zeros(lat.shape5, dtype=torch.complex128, device="cuda")
+    x, st = lat.solve(z, 0.1, 0.1)
+    assert torch.count_nonzero(x).item() == 0 and st["iters"] == 0
+    with pytest.raises(lib.OdwfError):
+        lat.solve(z, 0.0, 0.1)  # mass outside (0, 1]
+    with pytest.raises(lib.OdwfError) as e:
+        b = torch.from_numpy(inputs.gaussian_spinor5(lat.dims, lat.Ns, 7)).cuda()
+        lat.solve(b, 0.01, 0.01, opts=lib.solve_opts(tol=1e-10, maxiter=3))
+    assert e.value.code == lib.ODWF_ENOCONV
+    # the device stays usable after an error return
+    lat.solve(torch.from_numpy(inputs.gaussian_spinor5(lat.dims, lat.Ns, 8)).cuda(), 0.1, 0.1)
+
+
+TERMS = [oeofa.Term(-1, 0.05, 0.05, 0.1), oeofa.Term(+1, 0.05, 0.1, 1.0), oeofa.Term(-1, 1.0, 0.1, 1.0)]
+
+
+@pytest.mark.parametrize("term", TERMS)
+def test_eofa_action_force(lib, term):
+    dims, Ns = (4, 4, 4, 4), 8
+    lat, op, U, om = _setup(lib, dims, Ns, "zolo", 0.4, 5)
+    phi = inputs.gaussian_spinor(dims, 11)
+    spec = lib.TermSpec(term.chirality, term.m3, term.m4, term.m_den)
+    S, st = lat.action(spec, torch.from_numpy(phi).cuda(), opts=lib.solve_opts(tol=1e-12))
+    So, _ = oeofa.action(op, term, phi, tol=1e-12)
+    assert abs(S - So) < 1e-10 * abs(So)
+    F, _ = lat.force(spec, torch.from_numpy(phi).cuda(), opts=lib.solve_opts(tol=1e-12))
+    Fo, _ = oeofa.force(op, term, phi, tol=1e-12)
+    assert _rel(F.cpu().numpy(), Fo) < 1e-9
+
+
+@pytest.mark.parametrize("term", TERMS[:2])
+def test_eofa_heatbath(lib, term):
+    dims, Ns = (4, 4, 4, 4), 8
+    lat, op, U, om = _setup(lib, dims, Ns, "zolo", 0.4, 6)
+    eta = inputs.gaussian_spinor(dims, 12)
+    spec = lib.TermSpec(term.chirality, term.m3, term.m4, term.m_den)
+    phi, info = lat.heatbath(spec, torch.from_numpy(eta).cuda(), opts=lib.solve_opts(tol=1e-12))
+    ph = phi.cpu().numpy()
+    # phi^dag X phi = eta^dag eta (P eta), X applied by the oracle
+    Xphi = oeofa.term_apply(op, term, ph, tol=1e-13)
+    P = oeofa.projector(term.chirality)
+    peta = np.einsum("ij,...jc->...ic", P, eta)
+    assert abs(np.vdot(ph, Xphi).real / np.vdot(peta, peta).real - 1) < 1e-9
+    mref = term.m4 if term.chirality < 0 else term.m3
+    from oracle.rational import inv_sqrt_for_error
+    rat = inv_sqrt_for_error(0.98 * (1 + mref) / (1 + term.m_den), 1.0, 1e-11)
+    pho, _ = oeofa.heatbath(op, term, eta, rat, tol=1e-13)
+    assert _rel(ph, pho) < 1e-9
+
+
+@pytest.mark.parametrize("prec", ["double", "single"])
+def test_full_size_sampled_parity(lib, prec):
+    """16^3 x 32, Ns = 16 (the timed workload's lattice): D_T at 64 sampled sites vs the oracle."""
+    dims, Ns = (16, 16, 16, 32), 16
+    lat, op, U, om = _setup(lib, dims, Ns, "zolo", 0.3, 1000)
+    psi = inputs.gaussian_spinor5(dims, Ns, 1001)
+    got = lat.apply(torch.from_numpy(psi).cuda(), 0.01 / 2.6, 1.0, op="dt", prec=prec).cpu().numpy()
+    rng = np.random.default_rng(0)
+    sites = [(int(rng.integers(Ns)), int(rng.integers(32)), int(rng.integers(16)), int(rng.integers(16)),
+              int(rng.integers(16))) for _ in range(64)]
+    sites += [(0, 0, 0, 0, 0), (Ns - 1, 31, 15, 15, 15)]
+    ref = dt_at_sites(op, psi, 0.01 / 2.6, 1.0, sites)
+    g = np.array([got[s] for s in sites])
+    tol = 1e-12 if prec == "double" else 2e-6
+    assert _rel(g, ref) < tol
