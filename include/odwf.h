@@ -149,6 +149,19 @@ int eofa_heatbath(odwf_t* h, const eofa_term* term, const void* eta, void* phi,
 int odwf_profile_enable(odwf_t* h, int enable);
 int odwf_profile_read(odwf_t* h, int* keys, int* launches, double* total_ms, int* n_io);
 
+/* Mass-preconditioning term lists for (m, m)/(M, M), M <= 1 (host only, no GPU work):
+ *   ODWF_MP_NONE: Eq.(noMP)    2 terms {-, +}            (n_mh = 0)
+ *   ODWF_MP_OLD : Eq.(old_MP_N) 2N + 2 terms {-, +, ...}  (N = n_mh heavy masses, Eq.(old_MP) at N = 1)
+ *   ODWF_MP_NEW : Eq.(new_MP_N) N + 2 terms               (Eq.(new_MP) at N = 1)
+ * mh[] must increase strictly within (m, M). parity = 1 applies the parity operation P (swap the
+ * two mass columns of every factor: Eq.(noMP_P) and the parity partners of Section 2), which flips
+ * every chirality. Writes at most cap terms to out and the count to *n_out. */
+#define ODWF_MP_NONE 0
+#define ODWF_MP_OLD  1
+#define ODWF_MP_NEW  2
+int eofa_mp_terms(int scheme, double m, const double* mh, int n_mh, double M, int parity,
+                  eofa_term* out, int cap, int* n_out);
+
 /* k(m_j, m_i) of Eq.(k_ij) (c = 1, lambda = 0) and Omega_pm of Eq.(delta_ij) (host, out[Ns]). */
 double eofa_k(double mj, double mi);
 int    odwf_omega_vector(const odwf_t* h, int chirality, double* out);

@@ -28,7 +28,7 @@ _OP = {"dt": OP_DT, "ht": OP_HT, "dodwf": OP_DODWF, OP_DT: OP_DT, OP_HT: OP_HT, 
 # every entry point the C ABI declares
 EXPORTS = ["odwf_create", "odwf_destroy", "odwf_last_error", "odwf_set_gauge", "odwf_apply", "odwf_apply_dag",
            "eofa_solve", "eofa_solve_batch", "eofa_action", "eofa_force", "eofa_heatbath", "eofa_k",
-           "odwf_omega_vector", "odwf_profile_enable", "odwf_profile_read"]
+           "odwf_omega_vector", "odwf_profile_enable", "odwf_profile_read", "eofa_mp_terms"]
 
 
 class OdwfError(RuntimeError):
@@ -93,6 +93,7 @@ def load_library(path: str = LIB_PATH):
     lib.odwf_omega_vector.argtypes = [vp, i, dp]
     lib.odwf_profile_enable.argtypes = [vp, i]
     lib.odwf_profile_read.argtypes = [vp, ip, ip, dp, ip]
+    lib.eofa_mp_terms.argtypes = [i, d, dp, i, d, i, ctypes.POINTER(Term), i, ip]
     _lib = lib
     return lib
 
@@ -259,6 +260,22 @@ class ODWF:
         out = (ctypes.c_double * self.Ns)()
         self._check(self.lib.odwf_omega_vector(self.h, int(chirality), out))
         return list(out)
+
+
+MP_NONE, MP_OLD, MP_NEW = 0, 1, 2
+
+
+def mp_terms(scheme, m, mh, M, parity=False):
+    """Term list of a mass-preconditioning scheme (Eq.(noMP), Eq.(old_MP_N), Eq.(new_MP_N))."""
+    lib = load_library()
+    mh = list(mh)
+    arr = (ctypes.c_double * max(1, len(mh)))(*mh)
+    out = (Term * 64)()
+    n = ctypes.c_int(0)
+    rc = lib.eofa_mp_terms(int(scheme), float(m), arr, len(mh), float(M), 1 if parity else 0, out, 64, ctypes.byref(n))
+    if rc != 0:
+        raise OdwfError(rc, "eofa_mp_terms: invalid scheme or masses")
+    return [TermSpec(out[i].chirality, out[i].m3, out[i].m4, out[i].m_den) for i in range(n.value)]
 
 
 def eofa_k(mj, mi):

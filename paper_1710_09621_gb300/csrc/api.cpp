@@ -135,13 +135,28 @@ const SCoef* get_coef(odwf_s* h, double m1, double m2) {
         set_err(h, ODWF_EINVAL, "singular even-odd diagonal block A");
         return nullptr;
     }
-    // order: A+, A-, A+^-1, A-^-1, A+^T, A-^T, A+^-T, A-^-T ; each stored transposed (Mt[s'][s])
-    const Mat* mats[8];
+    // D_odwf = omega^{1/2} D_T omega^{1/2} (1 + L): N_pm = omega^{1/2} (1 + L_pm), W = omega^{1/2}
+    Mat Np(n * n, 0.0), Nm(n * n, 0.0), W(n * n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        const double sq = std::sqrt(h->omega[i]);
+        W[i * n + i] = sq;
+        Np[i * n + i] = sq;
+        Nm[i * n + i] = sq;
+        if (i >= 1) Np[i * n + (i - 1)] = sq;       // (L_+)_{i,i-1} = 1
+        if (i + 1 < n) Nm[i * n + (i + 1)] = sq;    // (L_-)_{i,i+1} = 1
+    }
+    Np[0 * n + (n - 1)] = -m1 * std::sqrt(h->omega[0]);
+    Nm[(n - 1) * n + 0] = -m2 * std::sqrt(h->omega[n - 1]);
+    // order: A+, A-, A+^-1, A-^-1, A+^T, A-^T, A+^-T, A-^-T, N+, N-, W, W, N+^T, N-^T;
+    // each stored transposed (Mt[s'][s])
+    const Mat* mats[kNumCoef];
     Mat ApT = transpose(Ap, n), AmT = transpose(Am, n), ApiT = transpose(Api, n), AmiT = transpose(Ami, n);
+    Mat NpT = transpose(Np, n), NmT = transpose(Nm, n);
     mats[0] = &Ap; mats[1] = &Am; mats[2] = &Api; mats[3] = &Ami;
     mats[4] = &ApT; mats[5] = &AmT; mats[6] = &ApiT; mats[7] = &AmiT;
-    std::vector<double> host(8 * n * n);
-    for (int k = 0; k < 8; ++k) {
+    mats[8] = &Np; mats[9] = &Nm; mats[10] = &W; mats[11] = &W; mats[12] = &NpT; mats[13] = &NmT;
+    std::vector<double> host((size_t)kNumCoef * n * n);
+    for (int k = 0; k < kNumCoef; ++k) {
         Mat t = transpose(*mats[k], n);
         std::memcpy(host.data() + (size_t)k * n * n, t.data(), sizeof(double) * n * n);
     }
@@ -366,7 +381,19 @@ static int apply_common(odwf_s* h, int op, double m1, double m2, const void* in,
     if (!c) return ODWF_EINVAL;
     Workspace& w = h->ws;
     void *ie = w.b_e, *io = w.b_o, *oe = w.x_e, *oo = w.x_o;
-    if (op == ODWF_OP_DODWF) return set_err(h, ODWF_EINVAL, "D_odwf apply is provided by apply_dodwf");
+    if (op == ODWF_OP_DODWF) {
+        // D_odwf = W D_T W N (N = omega^{1/2}(1 + L), W = omega^{1/2});  D_odwf^dag = N^T W D_T^dag W
+        const double* pre = c->dev + (size_t)(dag ? 10 : 8) * h->Ns * h->Ns;
+        const double* post = c->dev + (size_t)(dag ? 12 : 10) * h->Ns * h->Ns;
+        if ((rc = launch_pack5(h, (const double*)in, oe, oo, stg, 0, st))) return rc;
+        if ((rc = launch_smix(h, stg, oe, ie, pre, 1.0, st))) return rc;
+        if ((rc = launch_smix(h, stg, oo, io, pre, 1.0, st))) return rc;
+        if ((rc = apply_dt_parity(h, stg, c, dag, 0, io, ie, oe, st))) return rc;
+        if ((rc = apply_dt_parity(h, stg, c, dag, 1, ie, io, oo, st))) return rc;
+        if ((rc = launch_smix(h, stg, oe, ie, post, 1.0, st))) return rc;
+        if ((rc = launch_smix(h, stg, oo, io, post, 1.0, st))) return rc;
+        return launch_unpack5(h, ie, io, (double*)out, stg, 0, st);
+    }
     // H_T = g5 R5 D_T ; H_T^dag = H_T. D_T^dag = g5 (D_T with transposed M) g5.
     // For H_T: out = g5 R5 D_T in  -> pack in plainly, unpack with R5 g5.
     // For H_T^dag = D_T^dag R5 g5: pack with R5 g5, apply D_T^dag, unpack plainly.
@@ -453,5 +480,79 @@ extern "C" int odwf_profile_read(odwf_t* h, int* keys, int* launches, double* to
         ++i;
     }
     *n_io = i;
+    return ODWF_OK;
+}
+
+// ---- mass-preconditioning term lists (Section 2) ----------------------------------------------
+namespace {
+
+// (m3, m4)/(m1, m2) with m1 == m3 (chirality -) or m2 == m4 (chirality +), Eq.(m1m2_m3m4)
+bool make_term(double m3, double m4, double m1, double m2, eofa_term* t) {
+    if (m1 == m3 && m2 != m4) {
+        *t = eofa_term{-1, m3, m4, m2};
+        return true;
+    }
+    if (m2 == m4 && m1 != m3) {
+        *t = eofa_term{+1, m3, m4, m1};
+        return true;
+    }
+    return false;
+}
+
+}  // namespace
+
+extern "C" int eofa_mp_terms(int scheme, double m, const double* mh, int n_mh, double M, int parity,
+                             eofa_term* out, int cap, int* n_out) {
+    if (!n_out || (n_mh > 0 && !mh) || n_mh < 0) return ODWF_EINVAL;
+    if (!(m > 0.0 && m < M && M <= 1.0)) return ODWF_EINVAL;
+    std::vector<double> h(mh, mh + n_mh);
+    for (int i = 0; i < n_mh; ++i) {
+        if (!(h[i] > m && h[i] < M)) return ODWF_EINVAL;
+        if (i > 0 && !(h[i] > h[i - 1])) return ODWF_EINVAL;
+    }
+    // factors as (numerator pair, denominator pair)
+    std::vector<std::pair<std::pair<double, double>, std::pair<double, double>>> f;
+    if (scheme == ODWF_MP_NONE) {
+        if (n_mh != 0) return ODWF_EINVAL;
+        f.push_back({{m, m}, {m, M}});
+        f.push_back({{m, M}, {M, M}});
+    } else if (scheme == ODWF_MP_OLD) {
+        std::vector<double> ms;
+        ms.push_back(m);
+        for (double x : h) ms.push_back(x);
+        ms.push_back(M);
+        for (size_t i = 0; i + 1 < ms.size(); ++i) {
+            const double a = ms[i], b = ms[i + 1];
+            f.push_back({{a, a}, {a, b}});
+            f.push_back({{a, b}, {b, b}});
+        }
+    } else if (scheme == ODWF_MP_NEW) {
+        if (n_mh < 1) return ODWF_EINVAL;
+        std::pair<double, double> cur{m, m}, nxt{m, h[0]};
+        f.push_back({cur, nxt});
+        cur = nxt;
+        for (int i = 1; i <= n_mh; ++i) {
+            const double target = i < n_mh ? h[i] : M;
+            nxt = (i % 2 == 1) ? std::make_pair(target, cur.second) : std::make_pair(cur.first, target);
+            f.push_back({cur, nxt});
+            cur = nxt;
+        }
+        f.push_back({cur, {M, M}});
+    } else {
+        return ODWF_EINVAL;
+    }
+    int n = 0;
+    for (auto& fr : f) {
+        double m3 = fr.first.first, m4 = fr.first.second, m1 = fr.second.first, m2 = fr.second.second;
+        if (parity) {
+            std::swap(m3, m4);
+            std::swap(m1, m2);
+        }
+        eofa_term t;
+        if (!make_term(m3, m4, m1, m2, &t)) return ODWF_EINVAL;
+        if (out && n < cap) out[n] = t;
+        ++n;
+    }
+    *n_out = n;
     return ODWF_OK;
 }

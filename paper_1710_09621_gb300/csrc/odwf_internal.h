@@ -24,6 +24,7 @@
 namespace odwf {
 
 constexpr int kMaxNs = 32;
+constexpr int kNumCoef = 14;  // s-matrices per mass pair (see SCoef)
 
 // ---- Krylov solver state in device memory ------------------------------------------------------
 enum : int { FLAG_RUN = 0, FLAG_CONVERGED = 1, FLAG_UPDATE = 2, FLAG_BREAKDOWN = 3, FLAG_MAXITER = 4 };
@@ -84,8 +85,9 @@ struct HopArgs {
 
 // ---- host-side handle --------------------------------------------------------------------------
 struct SCoef {
-    // 8 transposed Ns x Ns matrices, in this order:
-    //  0 A_+(m1), 1 A_-(m2), 2 A_+^{-1}, 3 A_-^{-1}, 4 A_+^T, 5 A_-^T, 6 A_+^{-T}, 7 A_-^{-T}
+    // kNumCoef transposed Ns x Ns matrices, in this order:
+    //  0 A_+(m1), 1 A_-(m2), 2 A_+^{-1}, 3 A_-^{-1}, 4 A_+^T, 5 A_-^T, 6 A_+^{-T}, 7 A_-^{-T},
+    //  8 N_+ = omega^{1/2}(1 + L_+(m1)), 9 N_-, 10/11 omega^{1/2} (diagonal), 12 N_+^T, 13 N_-^T
     // "transposed" means stored as Mt[s'][s] = M[s][s'] so thread s reads consecutive words.
     double* dev = nullptr;
 };

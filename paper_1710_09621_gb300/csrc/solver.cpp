@@ -14,6 +14,8 @@
 // device; the host only polls the solver state every few iterations.
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -119,6 +121,7 @@ static int write_state(odwf_s* h, cudaStream_t st) {
 int solve_core(odwf_s* h, double m1, double m2, const odwf_solve_opts* opts_in, odwf_solve_stats* stats,
                cudaStream_t st) {
     const auto t0 = std::chrono::steady_clock::now();
+    const bool debug = std::getenv("ODWF_DEBUG") != nullptr;
     odwf_solve_opts o{1e-10, 100000, ODWF_PREC_DOUBLE, 0.1, 0.0};
     if (opts_in) o = *opts_in;
     if (!(o.tol > 0.0) || o.maxiter < 1) return set_err(h, ODWF_EINVAL, "bad solve options");
@@ -167,7 +170,7 @@ int solve_core(odwf_s* h, double m1, double m2, const odwf_solve_opts* opts_in, 
     if ((rc = cuda_check(h, cudaMemsetAsync(w.x_e, 0, b64, st), "memset"))) return rc;
     if ((rc = cuda_check(h, cudaMemcpyAsync(w.r64, w.bh, b64, cudaMemcpyDeviceToDevice, st), "copy"))) return rc;
     int iters = 0, updates = 0;
-    double pp_keep = 0.0;
+    double beta_keep = 0.0;
     bool converged = rr64 <= tol2;
     while (!converged) {
         // restart the inner iteration from the FP64 residual in r64
@@ -182,21 +185,18 @@ int solve_core(odwf_s* h, double m1, double m2, const odwf_solve_opts* opts_in, 
         hs.tol2 = (stg == ST_DOUBLE ? 0.81 : 0.25) * tol2;
         hs.delta2 = (stg == ST_DOUBLE) ? 0.0 : o.delta * o.delta;
         hs.maxiter = o.maxiter - iters;
-        hs.beta = 0.0;
-        if (updates > 0) {
-            // the search direction is kept across a residual replacement
-            hs.pp = pp_keep;
-            hs.alpha = rr64 / pp_keep;
-        }
+        // The cycle that stopped on a residual check had updated x and r with the last direction but
+        // not yet formed the next one. Form it from the replaced residual: p = S^dag r + beta' p with
+        // beta' = |r_true|^2 / |r_prev|^2 (Sleijpen & van der Vorst). First cycle: p = S^dag r.
+        hs.beta = (updates == 0) ? 0.0 : beta_keep;
         if ((rc = write_state(h, st))) return rc;
         if (updates == 0) {
-            // first cycle: p = S^dag r (with beta = 0 and p = 0)
             if ((rc = cuda_check(h, cudaMemsetAsync(f.p, 0, bi, st), "memset"))) return rc;
             if (stg == ST_HALF && (rc = cuda_check(h, cudaMemsetAsync(f.ps, 0, sizeof(float) * h->Vh * h->Ns, st), "memset")))
                 return rc;
-            if ((rc = k1(h, f, c, true, f.r, f.rs, h->state, st))) return rc;
-            if ((rc = k2b(h, f, c, st))) return rc;
         }
+        if ((rc = k1(h, f, c, true, f.r, f.rs, h->state, st))) return rc;
+        if ((rc = k2b(h, f, c, st))) return rc;
         // iterate until the device flags convergence, an update, a breakdown or maxiter
         int flag = FLAG_RUN;
         int chunk = 8;
@@ -213,6 +213,11 @@ int solve_core(odwf_s* h, double m1, double m2, const odwf_solve_opts* opts_in, 
             }
             if ((rc = read_state(h, st))) return rc;
             flag = h->state_host->flag;
+            if (debug) {
+                const CGState& d = *h->state_host;
+                std::fprintf(stderr, "[odwf] cycle %d iter %d flag %d rr %.6e pp %.6e alpha %.6e beta %.6e rr_max %.6e\n",
+                             updates, d.iter, d.flag, d.rr, d.pp, d.alpha, d.beta, d.rr_max);
+            }
             if (chunk < 64) chunk *= 2;
             if (o.max_seconds > 0) {
                 const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -229,7 +234,8 @@ int solve_core(odwf_s* h, double m1, double m2, const odwf_solve_opts* opts_in, 
             }
         }
         iters += h->state_host->iter;
-        pp_keep = h->state_host->pp;
+        // previous iterated |r|^2 = rr / beta (the device set beta = rr_new / rr_old)
+        const double rr_prev = h->state_host->beta > 0.0 ? h->state_host->rr / h->state_host->beta : 0.0;
         if (flag == FLAG_BREAKDOWN) {
             if (stats) {
                 sres.iters = iters;
@@ -242,6 +248,8 @@ int solve_core(odwf_s* h, double m1, double m2, const odwf_solve_opts* opts_in, 
         if ((rc = schur_residual64(h, c, w.bh, w.x_e, w.t64, w.r64, 3, st))) return rc;
         if ((rc = read_state(h, st))) return rc;
         rr64 = h->state_host->result[3];
+        beta_keep = rr_prev > 0.0 ? rr64 / rr_prev : 0.0;
+        if (debug) std::fprintf(stderr, "[odwf] update %d: true |r|^2 %.6e (tol2 %.6e), beta' %.6e\n", updates, rr64, tol2, beta_keep);
         ++updates;
         if (!std::isfinite(rr64)) return set_err(h, ODWF_EBREAKDOWN, "non-finite true residual");
         converged = rr64 <= tol2;

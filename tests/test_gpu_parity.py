@@ -66,6 +66,13 @@ def test_apply_dt_parity(lib, case, m12):
     assert _rel(goth, refh) < 1e-12
     gothd = lat.apply(x, *m12, op="ht", dag=True).cpu().numpy()
     assert _rel(gothd, refh) < 1e-12  # H_T is Hermitian
+    # D_odwf and its adjoint
+    refo = op.dodwf(psi, *m12)
+    goto = lat.apply(x, *m12, op="dodwf").cpu().numpy()
+    assert _rel(goto, refo) < 1e-12
+    a = inputs.gaussian_spinor5(case[0], case[1], 300 + case[4])
+    gota = lat.apply(torch.from_numpy(a).cuda(), *m12, op="dodwf", dag=True).cpu().numpy()
+    assert abs(np.vdot(a, refo) - np.vdot(gota, psi)) < 1e-11 * abs(np.vdot(a, refo))
 
 
 @pytest.mark.parametrize("case", CASES[:3])

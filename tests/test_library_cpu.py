@@ -35,3 +35,32 @@ def test_binding_fails_loudly_without_library(tmp_path):
         binding._lib = None
         binding.load_library(str(tmp_path / "missing.so"))
     binding._lib = None
+
+
+def test_mp_term_lists_match_oracle():
+    """The library's term lists (host code) equal the oracle's Eq.(noMP)/(old_MP_N)/(new_MP_N) lists."""
+    from paper_1710_09621_gb300 import binding, build
+    try:
+        build.build()
+    except RuntimeError as e:
+        pytest.skip(str(e))
+    from oracle import eofa
+
+    def key(ts):
+        return [(t.chirality, t.m3, t.m4, t.m_den) for t in ts]
+
+    m, M = 0.01, 1.0
+    assert key(binding.mp_terms(binding.MP_NONE, m, [], M)) == key(eofa.no_mp(m, M))
+    assert key(binding.mp_terms(binding.MP_OLD, m, [0.1], M)) == key(eofa.old_mp(m, 0.1, M))
+    assert key(binding.mp_terms(binding.MP_NEW, m, [0.1], M)) == key(eofa.new_mp(m, 0.1, M))
+    for hs in ([0.1, 0.3], [0.05, 0.1, 0.4]):
+        assert key(binding.mp_terms(binding.MP_OLD, m, hs, M)) == key(eofa.old_mp_cascade(m, hs, M))
+        assert key(binding.mp_terms(binding.MP_NEW, m, hs, M)) == key(eofa.new_mp_cascade(m, hs, M))
+        assert len(binding.mp_terms(binding.MP_NEW, m, hs, M)) == len(hs) + 2
+        assert len(binding.mp_terms(binding.MP_OLD, m, hs, M)) == 2 * len(hs) + 2
+    # parity partner of Eq.(noMP) is Eq.(noMP_P): chiralities {+, -}
+    pp = binding.mp_terms(binding.MP_NONE, m, [], M, parity=True)
+    assert [t.chirality for t in pp] == [1, -1]
+    assert key(pp) == key([eofa.term_from_ratio((m, m), (M, m)), eofa.term_from_ratio((M, m), (M, M))])
+    with pytest.raises(binding.OdwfError):
+        binding.mp_terms(binding.MP_NEW, m, [2.0], M)
