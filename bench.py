@@ -180,10 +180,14 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--ref-iters", type=int, default=1700)
+    ap.add_argument("--dims", default=None, help="override lattice, e.g. 16,16,16,16 (profiling only)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
 
+    global DIMS
+    if args.dims:
+        DIMS = tuple(int(v) for v in args.dims.split(","))
     import numpy as np
     import torch
     from paper_1710_09621_gb300 import build, inputs
