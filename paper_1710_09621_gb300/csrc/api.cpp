@@ -257,11 +257,19 @@ int odwf_create(odwf_t** out, const int dims[4], int Ns, double m0, const double
         lexof[p].resize(h->Vh);
         nbr[p].resize((size_t)h->Vh * 8);
     }
+    // Checkerboard order: the lattice is tiled by 2^4 blocks (all extents are even); block b holds
+    // the checkerboard indices 8b .. 8b+7 of each parity, lexicographic inside the block. A CTA of
+    // 8 (or 16) consecutive sites therefore covers one (two) whole blocks, and half of the
+    // neighbours it reads belong to its own block, which raises L1 reuse of the hopped field.
+    const int nbx = Lx / 2, nby = Ly / 2, nbz = Lz / 2;
     for (int lex = 0; lex < V; ++lex) {
         const int x = lex % Lx, y = (lex / Lx) % Ly, z = (lex / (Lx * Ly)) % Lz, t = lex / (Lx * Ly * Lz);
         const int p = (x + y + z + t) & 1;
-        lexof[p][lex / 2] = lex;
-        cbof[lex] = lex / 2;
+        const int b = (x / 2) + nbx * ((y / 2) + nby * ((z / 2) + nbz * (t / 2)));
+        const int inner = (x & 1) + 2 * ((y & 1) + 2 * ((z & 1) + 2 * (t & 1)));  // 0..15
+        const int cb = 8 * b + (inner >> 1);  // each parity takes every other inner index
+        lexof[p][cb] = lex;
+        cbof[lex] = cb;
     }
     for (int p = 0; p < 2; ++p)
         for (int cb = 0; cb < h->Vh; ++cb) {
