@@ -115,15 +115,14 @@ static bool m_matrix(const std::vector<double>& omega, double m, int c, Mat& M) 
     return true;
 }
 
-const SCoef* get_coef(odwf_s* h, double m1, double m2) {
-    auto key = std::make_pair(m1, m2);
-    auto it = h->coefs.find(key);
-    if (it != h->coefs.end()) return &it->second;
+// The kNumCoef fifth-dimension matrices of a mass pair, each stored transposed (Mt[s'][s]), in
+// the order documented at SCoef. Host FP64; returns false (with a message) if a block is singular.
+bool coef_host(const odwf_s* h, double m1, double m2, std::vector<double>& host, std::string& err) {
     const int n = h->Ns;
     Mat Mp, Mm;
     if (!m_matrix(h->omega, m1, +1, Mp) || !m_matrix(h->omega, m2, -1, Mm)) {
-        set_err(h, ODWF_EINVAL, "singular 1 + L in the fifth-dimension setup");
-        return nullptr;
+        err = "singular 1 + L in the fifth-dimension setup";
+        return false;
     }
     Mat Ap = Mp, Am = Mm;
     for (int i = 0; i < n; ++i) {
@@ -132,8 +131,8 @@ const SCoef* get_coef(odwf_s* h, double m1, double m2) {
     }
     Mat Api, Ami;
     if (!mat_inv(Ap, Api, n) || !mat_inv(Am, Ami, n)) {
-        set_err(h, ODWF_EINVAL, "singular even-odd diagonal block A");
-        return nullptr;
+        err = "singular even-odd diagonal block A";
+        return false;
     }
     // D_odwf = omega^{1/2} D_T omega^{1/2} (1 + L): N_pm = omega^{1/2} (1 + L_pm), W = omega^{1/2}
     Mat Np(n * n, 0.0), Nm(n * n, 0.0), W(n * n, 0.0);
@@ -147,18 +146,30 @@ const SCoef* get_coef(odwf_s* h, double m1, double m2) {
     }
     Np[0 * n + (n - 1)] = -m1 * std::sqrt(h->omega[0]);
     Nm[(n - 1) * n + 0] = -m2 * std::sqrt(h->omega[n - 1]);
-    // order: A+, A-, A+^-1, A-^-1, A+^T, A-^T, A+^-T, A-^-T, N+, N-, W, W, N+^T, N-^T;
-    // each stored transposed (Mt[s'][s])
+    // order: A+, A-, A+^-1, A-^-1, A+^T, A-^T, A+^-T, A-^-T, N+, N-, W, W, N+^T, N-^T
     const Mat* mats[kNumCoef];
     Mat ApT = transpose(Ap, n), AmT = transpose(Am, n), ApiT = transpose(Api, n), AmiT = transpose(Ami, n);
     Mat NpT = transpose(Np, n), NmT = transpose(Nm, n);
     mats[0] = &Ap; mats[1] = &Am; mats[2] = &Api; mats[3] = &Ami;
     mats[4] = &ApT; mats[5] = &AmT; mats[6] = &ApiT; mats[7] = &AmiT;
     mats[8] = &Np; mats[9] = &Nm; mats[10] = &W; mats[11] = &W; mats[12] = &NpT; mats[13] = &NmT;
-    std::vector<double> host((size_t)kNumCoef * n * n);
+    host.assign((size_t)kNumCoef * n * n, 0.0);
     for (int k = 0; k < kNumCoef; ++k) {
         Mat t = transpose(*mats[k], n);
         std::memcpy(host.data() + (size_t)k * n * n, t.data(), sizeof(double) * n * n);
+    }
+    return true;
+}
+
+const SCoef* get_coef(odwf_s* h, double m1, double m2) {
+    auto key = std::make_pair(m1, m2);
+    auto it = h->coefs.find(key);
+    if (it != h->coefs.end()) return &it->second;
+    std::vector<double> host;
+    std::string err;
+    if (!coef_host(h, m1, m2, host, err)) {
+        set_err(h, ODWF_EINVAL, err);
+        return nullptr;
     }
     SCoef c;
     if (cudaMalloc(&c.dev, sizeof(double) * host.size()) != cudaSuccess) {

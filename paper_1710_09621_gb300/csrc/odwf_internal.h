@@ -152,6 +152,9 @@ inline size_t half_elems_bytes(const odwf_s* h, int st) {
 int set_err(odwf_s* h, int code, const std::string& msg);
 int cuda_check(odwf_s* h, cudaError_t e, const char* what);
 const SCoef* get_coef(odwf_s* h, double m1, double m2);
+bool coef_host(const odwf_s* h, double m1, double m2, std::vector<double>& host, std::string& err);
+int apply_dt_parity(odwf_s* h, int stg, const SCoef* c, bool dag, int parity, const void* in_other,
+                    const void* own, void* out, cudaStream_t st);
 
 // launch helpers (kernels.cu)
 // Generic hop: out_p = epi( [MIXOWN ? Mown own : 0] + Mhop?( c_hop H in + a_own own ) )
