@@ -23,6 +23,7 @@ int solve_core(odwf_s* h, double m1, double m2, const odwf_solve_opts* opts, odw
                cudaStream_t st);
 
 static std::string g_create_err;
+int ensure_ws(odwf_s* h, Workspace& w, int inner);
 
 int set_err(odwf_s* h, int code, const std::string& msg) {
     if (h) h->err = msg;
@@ -194,8 +195,9 @@ static int alloc(odwf_s* h, void** p, size_t bytes) {
     return ODWF_OK;
 }
 
-int ensure_workspace(odwf_s* h, int inner) {
-    Workspace& w = h->ws;
+int ensure_workspace(odwf_s* h, int inner) { return ensure_ws(h, h->ws, inner); }
+
+int ensure_ws(odwf_s* h, Workspace& w, int inner) {
     const size_t b64 = half_elems_bytes(h, ST_DOUBLE);
     int rc;
     void** f64s[] = {&w.b_e, &w.b_o, &w.x_e, &w.x_o, &w.r64, &w.t64, &w.bh};
@@ -341,6 +343,15 @@ int odwf_destroy(odwf_t* h) {
     void* ps[] = {w.b_e, w.b_o, w.x_e, w.x_o, w.r64, w.t64, w.bh, w.xi, w.ri, w.pi, w.ti,
                   w.xi_s, w.ri_s, w.pi_s, w.ti_s, h->f64[0], h->f64[1], h->f64[2], h->f64[3], h->acc4};
     for (void* p : ps) cudaFree(p);
+    for (Workspace& b : h->bws) {
+        void* qs[] = {b.b_e, b.b_o, b.x_e, b.x_o, b.r64, b.t64, b.bh, b.xi, b.ri, b.pi, b.ti, b.xi_s, b.ri_s, b.pi_s, b.ti_s};
+        for (void* q : qs) cudaFree(q);
+    }
+    cudaFree(h->bstate);
+    cudaFree(h->bpartials);
+    cudaFree(h->bargs);
+    if (h->bstate_host) cudaFreeHost(h->bstate_host);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
     return ODWF_OK;
 }

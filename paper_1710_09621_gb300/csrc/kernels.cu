@@ -221,7 +221,7 @@ __device__ void grid_finalize(const HopArgs& a, double part) {
 //   v = gamma_5 v                                  (G5_OUT)
 //   epilogue EPI
 template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
-__global__ void __launch_bounds__(256) k_hop(HopArgs a) {
+__device__ __forceinline__ void hop_body(const HopArgs& a) {
     using S = Store<ST>;
     using R = typename S::R;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -352,6 +352,19 @@ __global__ void __launch_bounds__(256) k_hop(HopArgs a) {
     if (REDUCE) grid_finalize<EPI>(a, part);
 }
 
+template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
+__global__ void __launch_bounds__(256) k_hop(HopArgs a) {
+    hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(a);
+}
+
+// Several independent systems in one launch: blockIdx.y selects the system's arguments (its own
+// fields, lattice tables, solver state and reduction buffer); blockIdx.x strides over its sites.
+// Systems that are converged or waiting for a host-side update return at once.
+template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
+__global__ void __launch_bounds__(256) k_hop_multi(const HopArgs* __restrict__ args) {
+    hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(args[blockIdx.y]);
+}
+
 // ---- launch ------------------------------------------------------------------------------------
 // Sites per CTA: the CTA holds spb * Ns threads, a multiple of 32 and at least 128.
 int spb_for(int Ns) {
@@ -363,35 +376,71 @@ int spb_for(int Ns) {
     return spb;
 }
 
+// Lattice tables of handle h for output parity `parity`; reducing epilogues default to the
+// handle's own state and reduction buffer. A plain store keeps a.state as given (null: no
+// early-exit check on the solver flag).
+void hop_fill(odwf_s* h, int storage, int parity, HopArgs& a, bool reduces) {
+    a.links = (storage == ST_DOUBLE) ? (const void*)h->U64[parity] : (const void*)h->U32[parity];
+    a.nbr = h->nbr[parity];
+    a.Vh = h->Vh;
+    a.Ns = h->Ns;
+    if (a.partials == nullptr) a.partials = h->partials;
+    if (reduces && a.state == nullptr) a.state = h->state;
+}
+
 template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
-static int launch_one(odwf_s* h, int parity, HopArgs a, cudaStream_t st) {
+static int occupancy(odwf_s* h, bool multi, size_t* smem_out) {
     using R = typename Store<ST>::R;
-    auto fn = k_hop<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>;
     const int Ns = h->Ns, spb = spb_for(Ns);
     const size_t smem = sizeof(R) * ((size_t)(MIXHOP + MIXOWN) * 2 * Ns * Ns + (size_t)spb * Ns * 24);
-    static int occ_cache[kMaxNs + 1] = {0};
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        attr_set = true;
+    *smem_out = smem;
+    static int occ_cache[2][kMaxNs + 1] = {{0}};
+    static bool attr_set[2] = {false, false};
+    auto fn1 = k_hop<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>;
+    auto fnm = k_hop_multi<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>;
+    if (!attr_set[multi]) {
+        if (multi) cudaFuncSetAttribute(fnm, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        else cudaFuncSetAttribute(fn1, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        attr_set[multi] = true;
     }
-    int& occ = occ_cache[Ns];
+    int& occ = occ_cache[multi][Ns];
     if (occ == 0) {
         int o = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, Ns * spb, smem) != cudaSuccess || o < 1) o = 1;
+        cudaError_t e = multi ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fnm, Ns * spb, smem)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn1, Ns * spb, smem);
+        if (e != cudaSuccess || o < 1) o = 1;
         occ = o;
     }
+    return occ;
+}
+
+template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
+static int launch_multi_one(odwf_s* h, const HopArgs* dev_args, int n, int max_vh, cudaStream_t st) {
+    size_t smem = 0;
+    const int occ = occupancy<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(h, true, &smem);
+    const int spb = spb_for(h->Ns);
+    const int groups = (max_vh + spb - 1) / spb;
+    int gx = (h->num_sms * occ + n - 1) / n;
+    if (gx < h->num_sms) gx = h->num_sms;
+    if (gx > groups) gx = groups;
+    if (gx < 1) gx = 1;
+    if (EPI != EPI_STORE && gx > h->partials_n) return set_err(h, ODWF_EINVAL, "partials buffer too small");
+    k_hop_multi<ST, HOP, MIXHOP, OWN, MIXOWN, EPI><<<dim3(gx, n), dim3(h->Ns, spb), smem, st>>>(dev_args);
+    return cuda_check(h, cudaGetLastError(), "k_hop_multi launch");
+}
+
+template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
+static int launch_one(odwf_s* h, int parity, HopArgs a, cudaStream_t st) {
+    auto fn = k_hop<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>;
+    const int Ns = h->Ns, spb = spb_for(Ns);
+    size_t smem = 0;
+    const int occ = occupancy<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(h, false, &smem);
     const int groups = (h->Vh + spb - 1) / spb;
     int grid = h->num_sms * occ;
     if (grid > groups) grid = groups;
     if (grid < 1) grid = 1;
     if (EPI != EPI_STORE && grid > h->partials_n) return set_err(h, ODWF_EINVAL, "partials buffer too small");
-    a.links = (ST == ST_DOUBLE) ? (const void*)h->U64[parity] : (const void*)h->U32[parity];
-    a.nbr = h->nbr[parity];
-    a.Vh = h->Vh;
-    a.Ns = Ns;
-    a.partials = h->partials;
-    if (EPI != EPI_STORE && a.state == nullptr) a.state = h->state;
+    hop_fill(h, ST, parity, a, EPI != EPI_STORE);
     const int key = ST * 100000 + HOP * 10000 + MIXHOP * 1000 + OWN * 100 + MIXOWN * 10 + EPI;
     cudaEvent_t ev0 = nullptr;
     if (h->prof) prof_begin(h, key, st, &ev0);
@@ -417,6 +466,29 @@ static int launch_st(odwf_s* h, int parity, bool hop, bool mixhop, bool own, boo
     ODWF_CASE(false, false, true, true, EPI_STORE)      // out = Mown own (s-local)
 #undef ODWF_CASE
     return set_err(h, ODWF_EINVAL, "unsupported hop kernel variant");
+}
+
+template <int ST>
+static int launch_multi_st(odwf_s* h, bool mixhop, bool own, bool mixown, int epi, const HopArgs* dev_args, int n,
+                           int max_vh, cudaStream_t st) {
+#define ODWF_MCASE(MH, OW, MO, E)                                                                  \
+    if (mixhop == MH && own == OW && mixown == MO && epi == E)                                     \
+        return launch_multi_one<ST, true, MH, OW, MO, E>(h, dev_args, n, max_vh, st);
+    ODWF_MCASE(true, false, false, EPI_STORE)
+    ODWF_MCASE(false, true, true, EPI_CG_A)
+    ODWF_MCASE(false, true, true, EPI_CG_B)
+#undef ODWF_MCASE
+    return set_err(h, ODWF_EINVAL, "unsupported multi-system hop kernel variant");
+}
+
+int launch_hop_multi(odwf_s* h, int storage, bool mixhop, bool own, bool mixown, int epi, const HopArgs* dev_args,
+                     int n, int max_vh, cudaStream_t st) {
+    switch (storage) {
+        case ST_DOUBLE: return launch_multi_st<ST_DOUBLE>(h, mixhop, own, mixown, epi, dev_args, n, max_vh, st);
+        case ST_FLOAT: return launch_multi_st<ST_FLOAT>(h, mixhop, own, mixown, epi, dev_args, n, max_vh, st);
+        case ST_HALF: return launch_multi_st<ST_HALF>(h, mixhop, own, mixown, epi, dev_args, n, max_vh, st);
+    }
+    return set_err(h, ODWF_EINVAL, "bad storage");
 }
 
 int launch_hop(odwf_s* h, int storage, int parity, bool mixhop, bool own, bool mixown, int epi, HopArgs a,
@@ -616,12 +688,15 @@ int launch_axpy_to64(odwf_s* h, double a, const void* x, int st_in, const float*
     return cuda_check(h, cudaGetLastError(), "k_axpy_to64");
 }
 
-int launch_norm2(odwf_s* h, const void* v, int storage, const float* sc, int slot, cudaStream_t st) {
+int launch_norm2(odwf_s* h, const void* v, int storage, const float* sc, int slot, cudaStream_t st,
+                 CGState* state, double* partials) {
     int g = grid_1d(h, (size_t)h->Vh * h->Ns);
     if (g > h->partials_n) g = h->partials_n;
-    if (storage == ST_DOUBLE) k_norm2<ST_DOUBLE><<<g, 256, 0, st>>>(v, sc, h->state, h->partials, slot, h->Vh, h->Ns);
-    else if (storage == ST_FLOAT) k_norm2<ST_FLOAT><<<g, 256, 0, st>>>(v, sc, h->state, h->partials, slot, h->Vh, h->Ns);
-    else k_norm2<ST_HALF><<<g, 256, 0, st>>>(v, sc, h->state, h->partials, slot, h->Vh, h->Ns);
+    if (!state) state = h->state;
+    if (!partials) partials = h->partials;
+    if (storage == ST_DOUBLE) k_norm2<ST_DOUBLE><<<g, 256, 0, st>>>(v, sc, state, partials, slot, h->Vh, h->Ns);
+    else if (storage == ST_FLOAT) k_norm2<ST_FLOAT><<<g, 256, 0, st>>>(v, sc, state, partials, slot, h->Vh, h->Ns);
+    else k_norm2<ST_HALF><<<g, 256, 0, st>>>(v, sc, state, partials, slot, h->Vh, h->Ns);
     return cuda_check(h, cudaGetLastError(), "k_norm2");
 }
 

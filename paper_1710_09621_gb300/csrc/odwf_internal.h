@@ -130,6 +130,15 @@ struct odwf_s {
     void* f64[4] = {nullptr, nullptr, nullptr, nullptr};
     // 4D scratch
     double* acc4 = nullptr;
+    // batch-solve pools: per-system workspaces, solver states, reduction buffers, kernel arguments
+    std::vector<odwf::Workspace> bws;
+    odwf::CGState* bstate = nullptr;
+    odwf::CGState* bstate_host = nullptr;
+    double* bpartials = nullptr;
+    int bcap = 0;
+    odwf::HopArgs* bargs = nullptr;
+    int bargs_cap = 0;
+    cudaStream_t cap_stream = nullptr;   // non-default stream used only to capture CUDA graphs
     // kernel timing (odwf_profile_*)
     bool prof = false;
     struct ProfRec { int key; cudaEvent_t a, b; };
@@ -150,6 +159,8 @@ inline size_t half_elems_bytes(const odwf_s* h, int st) {
 }
 
 int set_err(odwf_s* h, int code, const std::string& msg);
+int ensure_ws(odwf_s* h, Workspace& w, int inner);
+int ensure_workspace(odwf_s* h, int inner);
 int cuda_check(odwf_s* h, cudaError_t e, const char* what);
 const SCoef* get_coef(odwf_s* h, double m1, double m2);
 bool coef_host(const odwf_s* h, double m1, double m2, std::vector<double>& host, std::string& err);
@@ -169,7 +180,11 @@ int launch_convert(odwf_s* h, const void* in, int st_in, const float* in_scale, 
                    float* out_scale, cudaStream_t st);
 int launch_axpy_to64(odwf_s* h, double a, const void* xin, int st_in, const float* xin_scale, double* y,
                      cudaStream_t st);
-int launch_norm2(odwf_s* h, const void* v, int storage, const float* scale, int slot, cudaStream_t st);
+int launch_norm2(odwf_s* h, const void* v, int storage, const float* scale, int slot, cudaStream_t st,
+                 CGState* state = nullptr, double* partials = nullptr);
+void hop_fill(odwf_s* h, int storage, int parity, HopArgs& a, bool reduces);
+int launch_hop_multi(odwf_s* h, int storage, bool mixhop, bool own, bool mixown, int epi, const HopArgs* dev_args,
+                     int n, int max_vh, cudaStream_t st);
 int launch_gauge(odwf_s* h, const double* U, cudaStream_t st);
 int launch_init_state(odwf_s* h, cudaStream_t st);
 void prof_begin(odwf_s* h, int key, cudaStream_t st, cudaEvent_t* a);

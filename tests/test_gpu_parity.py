@@ -182,3 +182,39 @@ def test_full_size_solve_sampled_residual(lib, prec):
     # sampled estimate of the global residual, with statistical slack
     est = np.sqrt(np.sum(np.abs(r) ** 2) * (b.size / 12) / len(sites))
     assert est <= 1e-9 * nb
+
+
+@pytest.mark.parametrize("prec", ["double", "single", "half"])
+def test_solve_batch_same_lattice(lib, prec):
+    """Terms of Eq.(new_MP) and two heat-bath-like pole masses on one gauge field, in one batch."""
+    dims, Ns = (4, 4, 4, 4), 8
+    lat, op, U, om = _setup(lib, dims, Ns, "zolo", 0.4, 9)
+    m12 = [(0.05, 0.05), (0.05, 0.1), (1.0, 0.1), (0.3, 0.07)]
+    bs = [inputs.gaussian_spinor5(dims, Ns, 400 + i) for i in range(len(m12))]
+    xs, stats = lat.solve_batch([torch.from_numpy(b).cuda() for b in bs], m12,
+                                opts=lib.solve_opts(tol=1e-10, prec=prec))
+    for b, x, (m1, m2), st in zip(bs, xs, m12, stats):
+        xr = x.cpu().numpy()
+        res = np.linalg.norm(b - op.ht(xr, m1, m2)) / np.linalg.norm(b)
+        assert st["true_residual"] <= 1e-10 and res <= 1.05e-10, (m1, m2, res)
+    # a batch of one equals the single solve
+    x1, st1 = lat.solve(torch.from_numpy(bs[0]).cuda(), *m12[0], opts=lib.solve_opts(tol=1e-10, prec=prec))
+    assert _rel(x1.cpu().numpy(), xs[0].cpu().numpy()) < 1e-8
+
+
+def test_solve_multi_uneven_lattices(lib):
+    """Systems on lattices of different sizes (same Ns) advance in one launch per step."""
+    cases = [((4, 4, 4, 4), 0), ((6, 2, 2, 2), 1), ((8, 4, 4, 6), 2)]
+    Ns = 8
+    lats, ops, bs = [], [], []
+    for dims, seed in cases:
+        lat, op, U, om = _setup(lib, dims, Ns, "zolo", 0.4, 20 + seed)
+        lats.append(lat)
+        ops.append(op)
+        bs.append(inputs.gaussian_spinor5(dims, Ns, 500 + seed))
+    m12 = [(0.05, 0.1), (0.1, 0.05), (0.02, 1.0)]
+    xs, stats = lib.solve_multi(lats, [torch.from_numpy(b).cuda() for b in bs], m12,
+                                opts=lib.solve_opts(tol=1e-10, prec="single"))
+    for op, b, x, (m1, m2) in zip(ops, bs, xs, m12):
+        res = np.linalg.norm(b - op.ht(x.cpu().numpy(), m1, m2)) / np.linalg.norm(b)
+        assert res <= 1.05e-10
