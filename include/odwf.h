@@ -118,10 +118,18 @@ int odwf_apply_dag(odwf_t* h, int op, double m1, double m2, const void* in, void
 int eofa_solve(odwf_t* h, double m1, double m2, const void* b, void* x,
                const odwf_solve_opts* opts, odwf_solve_stats* stats, void* stream);
 
-/* n independent solves H_T(m12[2i], m12[2i+1]) x[i] = b[i] on the same gauge field, with the
- * Krylov iterations of all systems interleaved on one stream (each kernel launch covers every
- * active system). stats: array of n (may be NULL). */
+/* n independent solves H_T(m12[2i], m12[2i+1]) x[i] = b[i] on the same gauge field (e.g. the
+ * terms of a mass-preconditioning scheme, Eq.(new_MP), or the poles of a heat-bath). The Krylov
+ * iterations of all systems advance in lockstep on one stream: each kernel launch covers every
+ * active system, and the chunk of iterations between host polls is one replayed CUDA graph.
+ * stats: array of n (may be NULL). */
 int eofa_solve_batch(odwf_t* h, int n, const double* m12, const void* const* b, void* const* x,
+                     const odwf_solve_opts* opts, odwf_solve_stats* stats, void* stream);
+
+/* Like eofa_solve_batch, but system i lives on its own handle hs[i] (lattices of different sizes,
+ * one shared Ns): H_T(m12[2i], m12[2i+1]) x[i] = b[i] on hs[i]. All systems advance together, one
+ * kernel launch per step covering every system. stats: array of n (may be NULL). */
+int eofa_solve_multi(odwf_t* const* hs, int n, const double* m12, const void* const* b, void* const* x,
                      const odwf_solve_opts* opts, odwf_solve_stats* stats, void* stream);
 
 /* S = phi^dag X phi for one term (phi: 4D device field; only the term's chirality is read).

@@ -28,7 +28,8 @@ _OP = {"dt": OP_DT, "ht": OP_HT, "dodwf": OP_DODWF, OP_DT: OP_DT, OP_HT: OP_HT, 
 # every entry point the C ABI declares
 EXPORTS = ["odwf_create", "odwf_destroy", "odwf_last_error", "odwf_set_gauge", "odwf_apply", "odwf_apply_dag",
            "eofa_solve", "eofa_solve_batch", "eofa_action", "eofa_force", "eofa_heatbath", "eofa_k",
-           "odwf_omega_vector", "odwf_profile_enable", "odwf_profile_read", "eofa_mp_terms"]
+           "odwf_omega_vector", "odwf_profile_enable", "odwf_profile_read", "eofa_mp_terms",
+           "eofa_solve_multi"]
 
 
 class OdwfError(RuntimeError):
@@ -94,6 +95,8 @@ def load_library(path: str = LIB_PATH):
     lib.odwf_profile_enable.argtypes = [vp, i]
     lib.odwf_profile_read.argtypes = [vp, ip, ip, dp, ip]
     lib.eofa_mp_terms.argtypes = [i, d, dp, i, d, i, ctypes.POINTER(Term), i, ip]
+    lib.eofa_solve_multi.argtypes = [ctypes.POINTER(vp), i, dp, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                     ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), vp]
     _lib = lib
     return lib
 
@@ -276,6 +279,26 @@ def mp_terms(scheme, m, mh, M, parity=False):
     if rc != 0:
         raise OdwfError(rc, "eofa_mp_terms: invalid scheme or masses")
     return [TermSpec(out[i].chirality, out[i].m3, out[i].m4, out[i].m_den) for i in range(n.value)]
+
+
+def solve_multi(lats, bs, m12, opts=None, stream=None):
+    """Solve H_T on several lattices (same Ns) in lockstep; returns (xs, stats list)."""
+    import torch
+    lib = load_library()
+    n = len(lats)
+    xs = [torch.empty_like(b) for b in bs]
+    for lat, b in zip(lats, bs):
+        lat._field(b, lat.shape5)
+    hs = (ctypes.c_void_p * n)(*[lat.h.value for lat in lats])
+    arr = (ctypes.c_double * (2 * n))(*[float(v) for pair in m12 for v in pair])
+    bp = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bs])
+    xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+    st = (SolveStats * n)()
+    o = opts if opts is not None else solve_opts()
+    rc = lib.eofa_solve_multi(hs, n, arr, bp, xp, ctypes.byref(o), st, _stream_ptr(stream))
+    if rc != 0:
+        raise OdwfError(rc, lib.odwf_last_error(lats[0].h).decode())
+    return xs, [s.as_dict() for s in st]
 
 
 def eofa_k(mj, mi):
