@@ -177,6 +177,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="single", choices=["single", "half", "double"])
+    ap.add_argument("--delta", type=float, default=0.1, help="reliable-update trigger of the inner solver")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--ref-iters", type=int, default=1700)
@@ -209,7 +210,7 @@ def main():
     b = b_host.to(dev)
     lat = ODWF(DIMS, NS, M0, om)
     lat.set_gauge(U)
-    opts = solve_opts(tol=TOL, prec=args.prec)
+    opts = solve_opts(tol=TOL, prec=args.prec, delta=args.delta)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -295,7 +296,7 @@ def main():
         "dtype": {"single": "f32 (FP64 reliable updates)", "half": "f16 storage/f32 (FP64 reliable updates)",
                   "double": "f64"}[args.prec],
         "data": "synthetic",
-        "config": dict(WORKLOAD, prec=args.prec, l2="inputs larger than L2 (each solve streams >1 GB)",
+        "config": dict(WORKLOAD, prec=args.prec, delta=args.delta, l2="inputs larger than L2 (each solve streams >1 GB)",
                        parallelism=f"replicas x{world}"),
         "solve": {"iters": stats[-1]["iters"], "reliable_updates": stats[-1]["reliable_updates"],
                   "true_residual": max(s["true_residual"] for s in stats)},
