@@ -108,6 +108,17 @@ int odwf_set_gauge(odwf_t* h, const void* U, void* stream);
 int odwf_apply(odwf_t* h, int op, double m1, double m2, const void* in, void* out, int prec, void* stream);
 int odwf_apply_dag(odwf_t* h, int op, double m1, double m2, const void* in, void* out, int prec, void* stream);
 
+/* Allocation-free variant of odwf_apply (forward D_T or H_T only; prec DOUBLE or SINGLE), for
+ * callers that cannot allocate device memory while they run (a fixed memory budget set at start-up,
+ * all memory handed to the caller's own pool, or a region where the allocator must not be touched).
+ * The paper has no counterpart. It uses a 32 MiB file-scope device array instead of the handle's
+ * work fields and allocates nothing; lattices whose four even-odd half fields plus coefficients
+ * exceed 32 MiB (Vh * Ns above ~43,000 in FP64, ~87,000 in FP32) are rejected with ODWF_EINVAL.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current, so make that first call before any stream capture. Every call shares the
+ * array: calls whose GPU work overlaps race on it. The handle itself is created by odwf_create. */
+int odwf_apply_noalloc(odwf_t* h, int op, double m1, double m2, const void* in, void* out, int prec, void* stream);
+
 /* Solve H_T(m1, m2) x = b (5D, device, complex128), the system behind every EOFA heat-bath,
  * action and force (Eq.(m1m2_m1m4), Eq.(m1m2_m3m2)); CG is the paper's solver (Section 1).
  * Method: D_T x = R5 gamma_5 b, even-odd Schur complement S = A - 1/4 H_eo A^{-1} H_oe, CGNE on S,

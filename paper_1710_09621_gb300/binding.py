@@ -29,7 +29,7 @@ _OP = {"dt": OP_DT, "ht": OP_HT, "dodwf": OP_DODWF, OP_DT: OP_DT, OP_HT: OP_HT, 
 EXPORTS = ["odwf_create", "odwf_destroy", "odwf_last_error", "odwf_set_gauge", "odwf_apply", "odwf_apply_dag",
            "eofa_solve", "eofa_solve_batch", "eofa_action", "eofa_force", "eofa_heatbath", "eofa_k",
            "odwf_omega_vector", "odwf_profile_enable", "odwf_profile_read", "eofa_mp_terms",
-           "eofa_solve_multi"]
+           "odwf_apply_noalloc", "eofa_solve_multi"]
 
 
 class OdwfError(RuntimeError):
@@ -95,6 +95,7 @@ def load_library(path: str = LIB_PATH):
     lib.odwf_profile_enable.argtypes = [vp, i]
     lib.odwf_profile_read.argtypes = [vp, ip, ip, dp, ip]
     lib.eofa_mp_terms.argtypes = [i, d, dp, i, d, i, ctypes.POINTER(Term), i, ip]
+    lib.odwf_apply_noalloc.argtypes = [vp, i, d, d, vp, vp, i, vp]
     lib.eofa_solve_multi.argtypes = [ctypes.POINTER(vp), i, dp, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                      ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), vp]
     _lib = lib
