@@ -89,7 +89,7 @@ class ClockSampler:
 # algorithmic bytes per launch of the fused hopping kernels (per 5D half-site: spinor reads and
 # writes of 24 reals, links 8 x 18 reals per 4D half-site shared by Ns slices)
 def alg_bytes(key, Vh, Ns):
-    st = key // 100000
+    st = (key // 100000) % 10
     hop, mixhop, own, mixown, epi = (key // 10000) % 10, (key // 1000) % 10, (key // 100) % 10, (key // 10) % 10, key % 10
     rb = {0: 8, 1: 4, 2: 2}[st]        # bytes per real of the spinor storage
     lb = 8 if st == 0 else 4           # link storage
@@ -114,12 +114,13 @@ def alg_bytes(key, Vh, Ns):
 
 
 def kernel_name(key):
-    st = ["fp64", "fp32", "fp16"][key // 100000]
+    st = ["fp64", "fp32", "fp16"][(key // 100000) % 10]
+    staged = "staged," if key >= 1000000 else ""
     hop, mixhop, own, mixown, epi = (key // 10000) % 10, (key // 1000) % 10, (key // 100) % 10, (key // 10) % 10, key % 10
     kind = {(1, 1, 0, 0): "hop+A^-1", (1, 0, 1, 1): "hop+A*own", (1, 1, 1, 0): "hop+own+A^-1",
             (1, 0, 1, 0): "hop+own", (0, 0, 1, 1): "s-mix"}.get((hop, mixhop, own, mixown), "hop")
     epin = ["store", "store+norm", "cg_a", "cg_b", "resid"][epi]
-    return f"k_hop<{st},{kind},{epin}>"
+    return f"k_hop<{staged}{st},{kind},{epin}>"
 
 
 def cpu_oracle_sample(n_full_iters):
@@ -177,7 +178,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="single", choices=["single", "half", "double"])
-    ap.add_argument("--delta", type=float, default=0.1, help="reliable-update trigger of the inner solver")
+    ap.add_argument("--delta", type=float, default=None,
+                    help="reliable-update trigger of the inner solver (default 0.01 FP32, 0.1 FP16)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--ref-iters", type=int, default=1700)
@@ -187,6 +189,8 @@ def main():
         return run_reference(args)
 
     global DIMS
+    if args.delta is None:
+        args.delta = 0.01 if args.prec == "single" else 0.1
     if args.dims:
         DIMS = tuple(int(v) for v in args.dims.split(","))
     import numpy as np

@@ -159,6 +159,37 @@ int eofa_force(odwf_t* h, const eofa_term* term, const void* phi, double* F,
 int eofa_heatbath(odwf_t* h, const eofa_term* term, const void* eta, void* phi,
                   odwf_hb_opts* opts, void* stream);
 
+/* ---- learned preconditioner (not in the paper) ----------------------------------------------
+ * A gauge-equivariant two-layer network of parallel-transport convolutions approximating S^{-1}
+ * for the even-odd Schur complement S of D_T(m1, m2) (the system eofa_solve iterates on):
+ *   u = A^{-1} r, v_c = A^{-1} sum_d W1[c,d] T_d u, M r = W0 u + 1/4 A^{-1} sum_{c,d} W2[c,d] T_d v_c,
+ * T_d = parallel transport by one link along d (4 forward, 4 backward), W = 4x4 complex spin
+ * matrices, c = 0..channels-1. Channel mixing runs on the tensor cores in BF16 with FP32
+ * accumulation; everything else in FP32. Weights (complex128, host): W0 [4][4], then W1
+ * [channels][8][4][4], then W2 [channels][8][4][4], each matrix [out spin][in spin]; the initial
+ * weights make M the two-term Neumann series A^{-1} + 1/4 A^{-1} H A^{-1} H A^{-1} of S^{-1}. */
+typedef struct odwf_net_s odwf_net_t;
+int odwf_net_create(odwf_t* h, int channels, odwf_net_t** net);      /* channels 1 or 2 */
+int odwf_net_destroy(odwf_net_t* net);
+int odwf_net_num_params(const odwf_net_t* net);                       /* complex parameters */
+int odwf_net_weights(odwf_net_t* net, double* host, int set);         /* set = 1 upload, 0 download */
+/* M r (adjoint = 0) or M^dag r (adjoint = 1); r, out: 5D ABI fields, only even sites read, odd
+ * sites of out set to zero. */
+int odwf_net_apply(odwf_net_t* net, double m1, double m2, const void* r, void* out, int adjoint, void* stream);
+/* Training pairs (r_i, e_i = S^{-1} r_i): r_i are 5D ABI fields (even sites used); if e is NULL the
+ * library solves for e_i itself (FP32 CGNE with FP64 reliable updates to tol). */
+int odwf_net_set_pairs(odwf_net_t* net, double m1, double m2, int npairs, const void* const* r,
+                       const void* const* e, double tol, void* stream);
+/* L = sum_i |M r_i - e_i|^2 / |e_i|^2 and dL/dconj(W) (host complex128, may be NULL). */
+int odwf_net_loss_grad(odwf_net_t* net, double* loss, double* grad, void* stream);
+/* steps Adam updates with learning rate lr on the stored pairs; losses[steps + 1] may be NULL. */
+int odwf_net_train(odwf_net_t* net, int steps, double lr, double* losses, void* stream);
+/* H_T(m1, m2) x = b like eofa_solve, with CGNE on S M (right preconditioning by the network, the
+ * iterate accumulating x = M y directly), FP32 inner cycles restarted from the FP64 residual
+ * whenever it has dropped by opts->delta. */
+int eofa_solve_learned(odwf_t* h, odwf_net_t* net, double m1, double m2, const void* b, void* x,
+                       const odwf_solve_opts* opts, odwf_solve_stats* stats, void* stream);
+
 /* Kernel timing for measurement: while enabled, every launch of the fused hopping kernels is
  * bracketed by CUDA events on its stream. odwf_profile_read synchronises the device and returns,
  * per kernel variant seen since the last enable, its key (storage*100000 + hop*10000 +

@@ -29,7 +29,9 @@ _OP = {"dt": OP_DT, "ht": OP_HT, "dodwf": OP_DODWF, OP_DT: OP_DT, OP_HT: OP_HT, 
 EXPORTS = ["odwf_create", "odwf_destroy", "odwf_last_error", "odwf_set_gauge", "odwf_apply", "odwf_apply_dag",
            "eofa_solve", "eofa_solve_batch", "eofa_action", "eofa_force", "eofa_heatbath", "eofa_k",
            "odwf_omega_vector", "odwf_profile_enable", "odwf_profile_read", "eofa_mp_terms",
-           "odwf_apply_noalloc", "eofa_solve_multi"]
+           "odwf_apply_noalloc", "eofa_solve_multi", "odwf_net_create", "odwf_net_destroy",
+           "odwf_net_num_params", "odwf_net_weights", "odwf_net_apply", "odwf_net_set_pairs", "odwf_net_loss_grad",
+           "odwf_net_train", "eofa_solve_learned"]
 
 
 class OdwfError(RuntimeError):
@@ -96,6 +98,15 @@ def load_library(path: str = LIB_PATH):
     lib.odwf_profile_read.argtypes = [vp, ip, ip, dp, ip]
     lib.eofa_mp_terms.argtypes = [i, d, dp, i, d, i, ctypes.POINTER(Term), i, ip]
     lib.odwf_apply_noalloc.argtypes = [vp, i, d, d, vp, vp, i, vp]
+    lib.odwf_net_create.argtypes = [vp, i, ctypes.POINTER(vp)]
+    lib.odwf_net_destroy.argtypes = [vp]
+    lib.odwf_net_num_params.argtypes = [vp]
+    lib.odwf_net_weights.argtypes = [vp, dp, i]
+    lib.odwf_net_apply.argtypes = [vp, d, d, vp, vp, i, vp]
+    lib.odwf_net_set_pairs.argtypes = [vp, d, d, i, ctypes.POINTER(vp), ctypes.POINTER(vp), d, vp]
+    lib.odwf_net_loss_grad.argtypes = [vp, dp, dp, vp]
+    lib.odwf_net_train.argtypes = [vp, i, d, dp, vp]
+    lib.eofa_solve_learned.argtypes = [vp, vp, d, d, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), vp]
     lib.eofa_solve_multi.argtypes = [ctypes.POINTER(vp), i, dp, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                      ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), vp]
     _lib = lib
@@ -280,6 +291,83 @@ def mp_terms(scheme, m, mh, M, parity=False):
     if rc != 0:
         raise OdwfError(rc, "eofa_mp_terms: invalid scheme or masses")
     return [TermSpec(out[i].chirality, out[i].m3, out[i].m4, out[i].m_den) for i in range(n.value)]
+
+
+class Net:
+    """Learned preconditioner of one lattice (see include/odwf.h); weights as complex numpy arrays."""
+
+    def __init__(self, lat, channels=2):
+        self.lat = lat
+        self.lib = lat.lib
+        n = ctypes.c_void_p()
+        lat._check(self.lib.odwf_net_create(lat.h, int(channels), ctypes.byref(n)))
+        self.n = n
+        self.C = int(channels)
+        self.P = self.lib.odwf_net_num_params(n)
+
+    def close(self):
+        if getattr(self, "n", None):
+            self.lib.odwf_net_destroy(self.n)
+            self.n = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_weights(self):
+        import numpy as np
+        buf = np.zeros(2 * self.P, dtype=np.float64)
+        self.lat._check(self.lib.odwf_net_weights(self.n, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0))
+        return buf.view(np.complex128).copy()
+
+    def set_weights(self, w):
+        import numpy as np
+        buf = np.ascontiguousarray(np.asarray(w, dtype=np.complex128).reshape(-1)).view(np.float64)
+        if buf.size != 2 * self.P:
+            raise ValueError("wrong number of parameters")
+        self.lat._check(self.lib.odwf_net_weights(self.n, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1))
+
+    def apply(self, r, m1, m2, adjoint=False, stream=None):
+        import torch
+        self.lat._field(r, self.lat.shape5)
+        out = torch.empty_like(r)
+        self.lat._check(self.lib.odwf_net_apply(self.n, float(m1), float(m2), _ptr(r), _ptr(out), 1 if adjoint else 0,
+                                                _stream_ptr(stream)))
+        return out
+
+    def set_pairs(self, rs, m1, m2, es=None, tol=1e-8, stream=None):
+        n = len(rs)
+        rp = (ctypes.c_void_p * n)(*[r.data_ptr() for r in rs])
+        ep = (ctypes.c_void_p * n)(*[e.data_ptr() for e in es]) if es is not None else None
+        self.lat._check(self.lib.odwf_net_set_pairs(self.n, float(m1), float(m2), n, rp, ep, float(tol),
+                                                    _stream_ptr(stream)))
+
+    def loss_grad(self, stream=None):
+        import numpy as np
+        L = ctypes.c_double()
+        g = np.zeros(2 * self.P, dtype=np.float64)
+        self.lat._check(self.lib.odwf_net_loss_grad(self.n, ctypes.byref(L), g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                    _stream_ptr(stream)))
+        return L.value, g.view(np.complex128).copy()
+
+    def train(self, steps, lr, stream=None):
+        import numpy as np
+        losses = np.zeros(steps + 1)
+        self.lat._check(self.lib.odwf_net_train(self.n, int(steps), float(lr),
+                                                losses.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream_ptr(stream)))
+        return losses
+
+    def solve(self, b, m1, m2, opts=None, stream=None):
+        import torch
+        self.lat._field(b, self.lat.shape5)
+        x = torch.empty_like(b)
+        st = SolveStats()
+        o = opts if opts is not None else solve_opts(prec="single", delta=1e-3)
+        self.lat._check(self.lib.eofa_solve_learned(self.lat.h, self.n, float(m1), float(m2), _ptr(b), _ptr(x),
+                                                    ctypes.byref(o), ctypes.byref(st), _stream_ptr(stream)))
+        return x, st.as_dict()
 
 
 def solve_multi(lats, bs, m12, opts=None, stream=None):

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libodwf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "eofa.cu", "solver.cpp", "api.cpp", "noalloc.cu"]
+SOURCES = ["kernels.cu", "eofa.cu", "solver.cpp", "api.cpp", "noalloc.cu", "learned.cu"]
 
 
 def nvcc() -> str:

@@ -8,6 +8,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -311,6 +312,9 @@ int odwf_create(odwf_t** out, const int dims[4], int Ns, double m0, const double
     h->partials_n = h->num_sms * 32;
     if (!rc) rc = alloc(h, (void**)&h->partials, sizeof(double) * h->partials_n);
     if (!rc) rc = alloc(h, (void**)&h->state, sizeof(CGState));
+    if (!rc) rc = alloc(h, (void**)&h->fault, sizeof(unsigned int));
+    if (!rc) rc = cuda_check(h, cudaMemset(h->fault, 0, sizeof(unsigned int)), "memset fault");
+    if (const char* e = std::getenv("ODWF_STAGED")) h->staged = (e[0] == '1') ? 1 : 0;
     if (!rc) rc = cuda_check(h, cudaMemset(h->state, 0, sizeof(CGState)), "memset state");
     if (!rc) rc = cuda_check(h, cudaMallocHost((void**)&h->state_host, sizeof(CGState)), "cudaMallocHost state");
     if (rc) {
@@ -338,6 +342,7 @@ int odwf_destroy(odwf_t* h) {
     for (auto e : h->prof_pool) cudaEventDestroy(e);
     cudaFree(h->partials);
     cudaFree(h->state);
+    cudaFree(h->fault);
     if (h->state_host) cudaFreeHost(h->state_host);
     Workspace& w = h->ws;
     void* ps[] = {w.b_e, w.b_o, w.x_e, w.x_o, w.r64, w.t64, w.bh, w.xi, w.ri, w.pi, w.ti,

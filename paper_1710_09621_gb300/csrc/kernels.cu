@@ -19,6 +19,8 @@
 
 namespace odwf {
 
+int spb_for(int Ns);
+
 // ---- complex helpers on interleaved real arrays ------------------------------------------------
 // spinor index of (spin, color) real part: (spin * 3 + color) * 2
 
@@ -220,6 +222,65 @@ __device__ void grid_finalize(const HopArgs& a, double part) {
 //   v += Mown own                                  (MIXOWN)
 //   v = gamma_5 v                                  (G5_OUT)
 //   epilogue EPI
+// Epilogue of the fused kernels for one (site, s): store, residual, or the CGNE updates; adds the
+// thread's contribution to the block reduction in `part`.
+template <int ST, int EPI>
+__device__ __forceinline__ void epilogue(const HopArgs& a, int cb, int s, typename Store<ST>::R* v,
+                                         const typename Store<ST>::R* ow, double alpha, double beta, double& part) {
+    using S = Store<ST>;
+    using R = typename S::R;
+    const int Ns = a.Ns;
+    if (EPI == EPI_STORE || EPI == EPI_STORE_NORM) {
+        S::store(a.out, a.out_scale, (size_t)cb, s, Ns, v);
+        if (EPI == EPI_STORE_NORM) {
+            R t = 0;
+#pragma unroll
+            for (int k = 0; k < 24; ++k) t = fma(v[k], v[k], t);
+            part += (double)t;
+        }
+    } else if (EPI == EPI_RESID) {
+        R b[24];
+        S::load(a.x, a.x_scale, (size_t)cb, s, Ns, b);
+        R t = 0;
+#pragma unroll
+        for (int k = 0; k < 24; ++k) {
+            b[k] -= v[k];
+            t = fma(b[k], b[k], t);
+        }
+        S::store(a.out, a.out_scale, (size_t)cb, s, Ns, b);
+        part += (double)t;
+    } else if (EPI == EPI_CG_A) {
+        // x += alpha * own (own = p, without gamma_5), r -= alpha * v
+        R x[24], r[24];
+        S::load(a.x, a.x_scale, (size_t)cb, s, Ns, x);
+        S::load(a.r, a.r_scale, (size_t)cb, s, Ns, r);
+        const R al = (R)alpha;
+        R t = 0;
+#pragma unroll
+        for (int k = 0; k < 24; ++k) {
+            x[k] = fma(al, ow[k], x[k]);
+            r[k] = fma(-al, v[k], r[k]);
+            t = fma(r[k], r[k], t);
+        }
+        S::store(a.x, a.x_scale, (size_t)cb, s, Ns, x);
+        S::store(a.r, a.r_scale, (size_t)cb, s, Ns, r);
+        part += (double)t;
+    } else if (EPI == EPI_CG_B) {
+        // p = v + beta * p
+        R p[24];
+        S::load(a.r, a.r_scale, (size_t)cb, s, Ns, p);
+        const R be = (R)beta;
+        R t = 0;
+#pragma unroll
+        for (int k = 0; k < 24; ++k) {
+            p[k] = fma(be, p[k], v[k]);
+            t = fma(p[k], p[k], t);
+        }
+        S::store(a.r, a.r_scale, (size_t)cb, s, Ns, p);
+        part += (double)t;
+    }
+}
+
 template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
 __device__ __forceinline__ void hop_body(const HopArgs& a) {
     using S = Store<ST>;
@@ -299,57 +360,300 @@ __device__ __forceinline__ void hop_body(const HopArgs& a) {
         if (g5out) g5_flip(v);
         if (!valid) continue;
 
-        if (EPI == EPI_STORE || EPI == EPI_STORE_NORM) {
-            S::store(a.out, a.out_scale, (size_t)cb, s, Ns, v);
-            if (EPI == EPI_STORE_NORM) {
-                R t = 0;
-#pragma unroll
-                for (int k = 0; k < 24; ++k) t = fma(v[k], v[k], t);
-                part += (double)t;
-            }
-        } else if (EPI == EPI_RESID) {
-            R b[24];
-            S::load(a.x, a.x_scale, (size_t)cb, s, Ns, b);
-            R t = 0;
-#pragma unroll
-            for (int k = 0; k < 24; ++k) {
-                b[k] -= v[k];
-                t = fma(b[k], b[k], t);
-            }
-            S::store(a.out, a.out_scale, (size_t)cb, s, Ns, b);
-            part += (double)t;
-        } else if (EPI == EPI_CG_A) {
-            // x += alpha * own (own = p, without gamma_5), r -= alpha * v
-            R x[24], r[24];
-            S::load(a.x, a.x_scale, (size_t)cb, s, Ns, x);
-            S::load(a.r, a.r_scale, (size_t)cb, s, Ns, r);
-            const R al = (R)alpha;
-            R t = 0;
-#pragma unroll
-            for (int k = 0; k < 24; ++k) {
-                x[k] = fma(al, ow[k], x[k]);
-                r[k] = fma(-al, v[k], r[k]);
-                t = fma(r[k], r[k], t);
-            }
-            S::store(a.x, a.x_scale, (size_t)cb, s, Ns, x);
-            S::store(a.r, a.r_scale, (size_t)cb, s, Ns, r);
-            part += (double)t;
-        } else if (EPI == EPI_CG_B) {
-            // p = v + beta * p
-            R p[24];
-            S::load(a.r, a.r_scale, (size_t)cb, s, Ns, p);
-            const R be = (R)beta;
-            R t = 0;
-#pragma unroll
-            for (int k = 0; k < 24; ++k) {
-                p[k] = fma(be, p[k], v[k]);
-                t = fma(p[k], p[k], t);
-            }
-            S::store(a.r, a.r_scale, (size_t)cb, s, Ns, p);
-            part += (double)t;
-        }
+        epilogue<ST, EPI>(a, cb, s, v, ow, alpha, beta, part);
     }
     if (REDUCE) grid_finalize<EPI>(a, part);
+}
+
+// ---- bulk-staged variant ------------------------------------------------------------------------
+// The same operator as hop_body, but the CTA first requests all the neighbour spinors it needs
+// with asynchronous bulk copies (cp.async.bulk, completion on one shared-memory mbarrier), so the
+// whole gather of a CTA is in flight at once instead of one dependent load per thread. A CTA owns
+// spb = 8k checkerboard sites = k whole 2^4 blocks (see the site order in odwf_create). Inside a
+// block every site has one neighbour per axis in the same block (the site with that coordinate
+// bit flipped: the whole other-parity half of the block, one contiguous run of 8 sites) and one
+// outside it (fetched individually through the neighbour table). Shared memory per CTA:
+//   slots [k*8 inside + 4*spb outside][NCH][Ns] 16-byte chunks (+ FP16 scales), the CTA's links
+//   [spb][8][20] floats, and the fifth-dimension matrices; the s-mixing buffer aliases the slots.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` for at most ~1 s of SM clock; false on time-out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > 2000000000LL) return false;
+    }
+    return true;
+}
+
+template <int ST>
+struct StagedGeom {
+    static constexpr int NCH = Store<ST>::NCH;
+    static __host__ __device__ int slot_bytes(int Ns) { return NCH * Ns * 16; }
+    static __host__ __device__ int scale_bytes(int Ns) { return ST == ST_HALF ? Ns * 4 : 0; }
+    static __host__ __device__ int nslots(int spb) { return spb + 4 * spb; }
+};
+
+// Spinor of slot `slot`, slice s, from shared memory (FP32 or FP16 chunks).
+template <int ST>
+__device__ __forceinline__ void slot_load(const unsigned char* slots, const float* scales, int slot, int s, int Ns,
+                                          float v[24]) {
+    if (ST == ST_FLOAT) {
+        const float4* p = reinterpret_cast<const float4*>(slots + (size_t)slot * StagedGeom<ST>::slot_bytes(Ns)) + s;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            float4 c = p[j * Ns];
+            v[4 * j] = c.x;
+            v[4 * j + 1] = c.y;
+            v[4 * j + 2] = c.z;
+            v[4 * j + 3] = c.w;
+        }
+    } else {
+        const uint4* p = reinterpret_cast<const uint4*>(slots + (size_t)slot * StagedGeom<ST>::slot_bytes(Ns)) + s;
+        const float sc = scales[slot * Ns + s];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            uint4 c = p[j * Ns];
+            const __half2* hh = reinterpret_cast<const __half2*>(&c);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float2 f = __half22float2(hh[q]);
+                v[8 * j + 2 * q] = f.x * sc;
+                v[8 * j + 2 * q + 1] = f.y * sc;
+            }
+        }
+    }
+}
+
+template <int ST, int MU>
+__device__ __forceinline__ void hop_dir_staged(const unsigned char* slots, const float* scales, const float* lk,
+                                               int spb, int ls, int s, int Ns, const int bits[4], bool g5in,
+                                               float* v) {
+    float psi[24], h[12], w[12], u[18];
+    const int blk = ls >> 3, i = ls & 7;
+    const int partner = blk * 8 + (MU == 0 ? i : (i ^ (1 << (MU - 1))));
+    const int outside = spb + ls * 4 + MU;
+    // forward neighbour is in the block iff the site's MU coordinate bit is 0
+    const int sf = bits[MU] == 0 ? partner : outside;
+    const int sb = bits[MU] == 1 ? partner : outside;
+    slot_load<ST>(slots, scales, sf, s, Ns, psi);
+    if (g5in) g5_flip(psi);
+    project<MU, -1>(psi, h);
+#pragma unroll
+    for (int k = 0; k < 18; ++k) u[k] = lk[(ls * 8 + MU) * 20 + k];
+    su3_mul_half(u, h, w);
+    reconstruct<MU, -1>(v, w);
+    slot_load<ST>(slots, scales, sb, s, Ns, psi);
+    if (g5in) g5_flip(psi);
+    project<MU, +1>(psi, h);
+#pragma unroll
+    for (int k = 0; k < 18; ++k) u[k] = lk[(ls * 8 + 4 + MU) * 20 + k];
+    su3_mul_half(u, h, w);
+    reconstruct<MU, +1>(v, w);
+}
+
+template <int ST, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
+__device__ __forceinline__ void hop_body_staged(const HopArgs& a) {
+    static_assert(ST == ST_FLOAT || ST == ST_HALF, "staged kernels are FP32 / FP16 storage");
+    using S = Store<ST>;
+    using G = StagedGeom<ST>;
+    extern __shared__ __align__(16) unsigned char smem_st[];
+    unsigned char* smem_raw = smem_st;
+    const int Ns = a.Ns;
+    const int s = threadIdx.x, ls = threadIdx.y, spb = blockDim.y;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+    const int SB = G::slot_bytes(Ns), SCB = G::scale_bytes(Ns), NSL = G::nslots(spb);
+    // layout: [mbarrier 16][matrices][links][slots][scales]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    float* mh = reinterpret_cast<float*>(smem_raw + 16);
+    float* mo = mh + (MIXHOP ? 2 * Ns * Ns : 0);
+    float* lk = mo + (MIXOWN ? 2 * Ns * Ns : 0);
+    unsigned char* slots = reinterpret_cast<unsigned char*>(lk + spb * 8 * 20);
+    float* scales = reinterpret_cast<float*>(slots + (size_t)NSL * SB);
+    float* sh = reinterpret_cast<float*>(slots);  // s-mixing buffer, reused after the hop
+    __shared__ int ok_s;
+    constexpr bool REDUCE = (EPI != EPI_STORE);
+
+    if (a.state != nullptr && EPI != EPI_STORE_NORM && EPI != EPI_RESID) {
+        if (((volatile CGState*)a.state)->flag != FLAG_RUN) return;
+    }
+    if (tid == 0) mbar_init(bar);
+    for (int i = tid; i < 2 * Ns * Ns; i += nth) {
+        if (MIXHOP) mh[i] = (float)a.mhop[i];
+        if (MIXOWN) mo[i] = (float)a.mown[i];
+    }
+    __syncthreads();
+    double alpha = 0.0, beta = 0.0;
+    if (EPI == EPI_CG_A) alpha = a.state->alpha;
+    if (EPI == EPI_CG_B) beta = a.state->beta;
+    const bool g5h = (a.g5 & G5_HOP_IN) != 0, g5o = (a.g5 & G5_OWN_IN) != 0, g5out = (a.g5 & G5_OUT) != 0;
+    const float chop = (float)a.c_hop, aown = (float)a.a_own;
+    double part = 0.0;
+    // site coordinate bits inside its 2^4 block (block-local index i = cb & 7: y, z, t bits; x from parity)
+    int bits[4];
+    {
+        const int i = ls & 7;
+        bits[1] = i & 1;
+        bits[2] = (i >> 1) & 1;
+        bits[3] = (i >> 2) & 1;
+        bits[0] = (a.parity ^ bits[1] ^ bits[2] ^ bits[3]) & 1;
+    }
+    uint32_t phase = 0;
+    const char* in_base = reinterpret_cast<const char*>(a.in);
+    const char* in_scale = reinterpret_cast<const char*>(a.in_scale);
+    const char* lk_base = reinterpret_cast<const char*>(a.links);
+
+    for (int g = blockIdx.x; g * spb < a.Vh; g += gridDim.x) {
+        // order this thread's generic shared-memory accesses before the next bulk copies
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();  // every thread is done with the previous group's shared memory
+        const int cb0 = g * spb;
+        const int nv = min(spb, a.Vh - cb0);  // a multiple of 8
+        const int nblk = nv >> 3;
+        const int cb = cb0 + ls;
+        const bool valid = ls < nv;
+        if (tid < 32) {
+            // warp 0 issues the gather: inside runs, outside singles, links (+ FP16 scales)
+            const int n_in = nblk, n_out = 4 * nv;
+            const int ncopy = (n_in + n_out) * (ST == ST_HALF ? 2 : 1) + 1;
+            if (tid == 0) {
+                const uint32_t total = (uint32_t)((size_t)(nblk * 8 + n_out) * (SB + SCB) + (size_t)nv * 8 * 80);
+                mbar_expect(bar, total);
+            }
+            __syncwarp();
+            for (int k = tid; k < ncopy; k += 32) {
+                int kk = k;
+                const bool sc = (ST == ST_HALF) && kk >= n_in + n_out + 1;
+                if (sc) kk -= n_in + n_out + 1;
+                if (!sc && kk == n_in + n_out) {
+                    bulk_copy(lk, lk_base + (size_t)cb0 * 8 * 80, (uint32_t)(nv * 8 * 80), bar);
+                    continue;
+                }
+                int src_cb, slot, count;
+                if (kk < n_in) {
+                    src_cb = cb0 + kk * 8;
+                    slot = kk * 8;
+                    count = 8;
+                } else {
+                    const int q = kk - n_in, site = q >> 2, mu = q & 3;
+                    const int i = site & 7;
+                    int b[4];
+                    b[1] = i & 1;
+                    b[2] = (i >> 1) & 1;
+                    b[3] = (i >> 2) & 1;
+                    b[0] = (a.parity ^ b[1] ^ b[2] ^ b[3]) & 1;
+                    const int dir = b[mu] ? mu : 4 + mu;  // the neighbour outside the block
+                    src_cb = __ldg(a.nbr + (size_t)(cb0 + site) * 8 + dir);
+                    slot = spb + site * 4 + mu;
+                    count = 1;
+                }
+                if (!sc)
+                    bulk_copy(slots + (size_t)slot * SB, in_base + (size_t)src_cb * SB, (uint32_t)(count * SB), bar);
+                else
+                    bulk_copy(scales + (size_t)slot * Ns, in_scale + (size_t)src_cb * SCB, (uint32_t)(count * SCB), bar);
+            }
+        }
+        // own field (streamed) while the gather is in flight
+        float ow[24];
+        if (OWN) {
+            if (valid) {
+                S::load(a.own, a.own_scale, (size_t)cb, s, Ns, ow);
+                if (g5o) g5_flip(ow);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 24; ++k) ow[k] = 0;
+            }
+        }
+        if (tid == 0) {
+            bool ok = mbar_wait_bounded(bar, phase);
+            if (!ok) {
+                if (a.fault) atomicOr(a.fault, 1u);
+                mbar_wait_bounded(bar, phase);  // give copies still in flight a last chance to land
+            }
+            ok_s = ok;
+        }
+        __syncthreads();
+        if (!ok_s) return;
+        phase ^= 1u;
+        float v[24];
+#pragma unroll
+        for (int k = 0; k < 24; ++k) v[k] = 0;
+        if (valid) {
+            hop_dir_staged<ST, 0>(slots, scales, lk, spb, ls, s, Ns, bits, g5h, v);
+            hop_dir_staged<ST, 1>(slots, scales, lk, spb, ls, s, Ns, bits, g5h, v);
+            hop_dir_staged<ST, 2>(slots, scales, lk, spb, ls, s, Ns, bits, g5h, v);
+            hop_dir_staged<ST, 3>(slots, scales, lk, spb, ls, s, Ns, bits, g5h, v);
+#pragma unroll
+            for (int k = 0; k < 24; ++k) v[k] *= chop;
+        }
+        if (OWN && !MIXOWN) {
+#pragma unroll
+            for (int k = 0; k < 24; ++k) v[k] = fma(aown, ow[k], v[k]);
+        }
+        __syncthreads();  // slots are read; the mixing buffer may overwrite them
+        if (MIXHOP) {
+            float* dst = sh + (ls * Ns + s) * 24;
+#pragma unroll
+            for (int k = 0; k < 24; ++k) dst[k] = v[k];
+            __syncthreads();
+            s_mix(mh, sh + ls * Ns * 24, s, Ns, v, false);
+        }
+        if (MIXOWN) {
+            if (MIXHOP) __syncthreads();
+            float* dst = sh + (ls * Ns + s) * 24;
+#pragma unroll
+            for (int k = 0; k < 24; ++k) dst[k] = ow[k];
+            __syncthreads();
+            s_mix(mo, sh + ls * Ns * 24, s, Ns, v, true);
+        }
+        if (g5out) g5_flip(v);
+        if (!valid) continue;
+        epilogue<ST, EPI>(a, cb, s, v, ow, alpha, beta, part);
+    }
+    if (REDUCE) grid_finalize<EPI>(a, part);
+}
+
+template <int ST, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
+__global__ void __launch_bounds__(256) k_hop_staged(HopArgs a) {
+    hop_body_staged<ST, MIXHOP, OWN, MIXOWN, EPI>(a);
+}
+
+template <int ST, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
+__global__ void __launch_bounds__(256) k_hop_staged_multi(const HopArgs* __restrict__ args) {
+    hop_body_staged<ST, MIXHOP, OWN, MIXOWN, EPI>(args[blockIdx.y]);
+}
+
+template <int ST>
+size_t staged_smem(int Ns, int spb, bool mixhop, bool mixown) {
+    using G = StagedGeom<ST>;
+    return 16 + sizeof(float) * (size_t)(mixhop + mixown) * 2 * Ns * Ns + (size_t)spb * 8 * 80 +
+           (size_t)G::nslots(spb) * (G::slot_bytes(Ns) + G::scale_bytes(Ns));
 }
 
 template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
@@ -384,31 +688,55 @@ void hop_fill(odwf_s* h, int storage, int parity, HopArgs& a, bool reduces) {
     a.nbr = h->nbr[parity];
     a.Vh = h->Vh;
     a.Ns = h->Ns;
+    a.parity = parity;
+    a.fault = h->fault;
     if (a.partials == nullptr) a.partials = h->partials;
     if (reduces && a.state == nullptr) a.state = h->state;
 }
 
+// The bulk-staged kernels need CTAs of whole 2^4 blocks (spb a multiple of 8) and, for FP16,
+// 16-byte scale rows (Ns a multiple of 4).
+static bool staged_ok(const odwf_s* h, int st) {
+    if (!h->staged || st == ST_DOUBLE) return false;
+    if (spb_for(h->Ns) % 8) return false;
+    if (st == ST_HALF && h->Ns % 4) return false;
+    return true;
+}
+
 template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
-static int occupancy(odwf_s* h, bool multi, size_t* smem_out) {
+struct KernelPick {
+    static constexpr bool CAN_STAGE = HOP && ST != ST_DOUBLE;
+    // kind: 0 plain single, 1 plain multi, 2 staged single, 3 staged multi
+    static const void* fn(int kind) {
+        if constexpr (CAN_STAGE) {
+            if (kind == 2) return (const void*)k_hop_staged<ST, MIXHOP, OWN, MIXOWN, EPI>;
+            if (kind == 3) return (const void*)k_hop_staged_multi<ST, MIXHOP, OWN, MIXOWN, EPI>;
+        }
+        return kind == 1 ? (const void*)k_hop_multi<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>
+                         : (const void*)k_hop<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>;
+    }
+};
+
+template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
+static int occupancy(odwf_s* h, int kind, size_t* smem_out) {
     using R = typename Store<ST>::R;
     const int Ns = h->Ns, spb = spb_for(Ns);
-    const size_t smem = sizeof(R) * ((size_t)(MIXHOP + MIXOWN) * 2 * Ns * Ns + (size_t)spb * Ns * 24);
-    *smem_out = smem;
-    static int occ_cache[2][kMaxNs + 1] = {{0}};
-    static bool attr_set[2] = {false, false};
-    auto fn1 = k_hop<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>;
-    auto fnm = k_hop_multi<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>;
-    if (!attr_set[multi]) {
-        if (multi) cudaFuncSetAttribute(fnm, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        else cudaFuncSetAttribute(fn1, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        attr_set[multi] = true;
+    size_t smem = sizeof(R) * ((size_t)(MIXHOP + MIXOWN) * 2 * Ns * Ns + (size_t)spb * Ns * 24);
+    if constexpr (ST != ST_DOUBLE) {
+        if (kind >= 2) smem = staged_smem<ST>(Ns, spb, MIXHOP, MIXOWN);
     }
-    int& occ = occ_cache[multi][Ns];
+    *smem_out = smem;
+    static int occ_cache[4][kMaxNs + 1] = {{0}};
+    static bool attr_set[4] = {false, false, false, false};
+    const void* fn = KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::fn(kind);
+    if (!attr_set[kind]) {
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set[kind] = true;
+    }
+    int& occ = occ_cache[kind][Ns];
     if (occ == 0) {
         int o = 0;
-        cudaError_t e = multi ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fnm, Ns * spb, smem)
-                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn1, Ns * spb, smem);
-        if (e != cudaSuccess || o < 1) o = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, Ns * spb, smem) != cudaSuccess || o < 1) o = 1;
         occ = o;
     }
     return occ;
@@ -417,7 +745,9 @@ static int occupancy(odwf_s* h, bool multi, size_t* smem_out) {
 template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
 static int launch_multi_one(odwf_s* h, const HopArgs* dev_args, int n, int max_vh, cudaStream_t st) {
     size_t smem = 0;
-    const int occ = occupancy<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(h, true, &smem);
+    const bool stg = KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::CAN_STAGE && staged_ok(h, ST);
+    const int kind = stg ? 3 : 1;
+    const int occ = occupancy<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(h, kind, &smem);
     const int spb = spb_for(h->Ns);
     const int groups = (max_vh + spb - 1) / spb;
     int gx = (h->num_sms * occ + n - 1) / n;
@@ -425,26 +755,37 @@ static int launch_multi_one(odwf_s* h, const HopArgs* dev_args, int n, int max_v
     if (gx > groups) gx = groups;
     if (gx < 1) gx = 1;
     if (EPI != EPI_STORE && gx > h->partials_n) return set_err(h, ODWF_EINVAL, "partials buffer too small");
+    if constexpr (KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::CAN_STAGE) {
+        if (stg) {
+            k_hop_staged_multi<ST, MIXHOP, OWN, MIXOWN, EPI><<<dim3(gx, n), dim3(h->Ns, spb), smem, st>>>(dev_args);
+            return cuda_check(h, cudaGetLastError(), "k_hop_staged_multi launch");
+        }
+    }
     k_hop_multi<ST, HOP, MIXHOP, OWN, MIXOWN, EPI><<<dim3(gx, n), dim3(h->Ns, spb), smem, st>>>(dev_args);
     return cuda_check(h, cudaGetLastError(), "k_hop_multi launch");
 }
 
 template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
 static int launch_one(odwf_s* h, int parity, HopArgs a, cudaStream_t st) {
-    auto fn = k_hop<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>;
     const int Ns = h->Ns, spb = spb_for(Ns);
     size_t smem = 0;
-    const int occ = occupancy<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(h, false, &smem);
+    const bool stg = KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::CAN_STAGE && staged_ok(h, ST);
+    const int occ = occupancy<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(h, stg ? 2 : 0, &smem);
     const int groups = (h->Vh + spb - 1) / spb;
     int grid = h->num_sms * occ;
     if (grid > groups) grid = groups;
     if (grid < 1) grid = 1;
     if (EPI != EPI_STORE && grid > h->partials_n) return set_err(h, ODWF_EINVAL, "partials buffer too small");
     hop_fill(h, ST, parity, a, EPI != EPI_STORE);
-    const int key = ST * 100000 + HOP * 10000 + MIXHOP * 1000 + OWN * 100 + MIXOWN * 10 + EPI;
+    const int key = (stg ? 1000000 : 0) + ST * 100000 + HOP * 10000 + MIXHOP * 1000 + OWN * 100 + MIXOWN * 10 + EPI;
     cudaEvent_t ev0 = nullptr;
     if (h->prof) prof_begin(h, key, st, &ev0);
-    fn<<<grid, dim3(Ns, spb), smem, st>>>(a);
+    if constexpr (KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::CAN_STAGE) {
+        if (stg) k_hop_staged<ST, MIXHOP, OWN, MIXOWN, EPI><<<grid, dim3(Ns, spb), smem, st>>>(a);
+        else k_hop<ST, HOP, MIXHOP, OWN, MIXOWN, EPI><<<grid, dim3(Ns, spb), smem, st>>>(a);
+    } else {
+        k_hop<ST, HOP, MIXHOP, OWN, MIXOWN, EPI><<<grid, dim3(Ns, spb), smem, st>>>(a);
+    }
     if (h->prof) prof_end(h, key, st, ev0);
     return cuda_check(h, cudaGetLastError(), "k_hop launch");
 }
@@ -497,6 +838,15 @@ int launch_hop(odwf_s* h, int storage, int parity, bool mixhop, bool own, bool m
         case ST_DOUBLE: return launch_st<ST_DOUBLE>(h, parity, true, mixhop, own, mixown, epi, a, st);
         case ST_FLOAT: return launch_st<ST_FLOAT>(h, parity, true, mixhop, own, mixown, epi, a, st);
         case ST_HALF: return launch_st<ST_HALF>(h, parity, true, mixhop, own, mixown, epi, a, st);
+    }
+    return set_err(h, ODWF_EINVAL, "bad storage");
+}
+
+// p = a_own * own + beta p with |p|^2 and the CGNE alpha update (no hop, no s-mixing)
+int launch_hop_own_cgb(odwf_s* h, int storage, HopArgs a, cudaStream_t st) {
+    switch (storage) {
+        case ST_DOUBLE: return launch_one<ST_DOUBLE, false, false, true, false, EPI_CG_B>(h, 0, a, st);
+        case ST_FLOAT: return launch_one<ST_FLOAT, false, false, true, false, EPI_CG_B>(h, 0, a, st);
     }
     return set_err(h, ODWF_EINVAL, "bad storage");
 }

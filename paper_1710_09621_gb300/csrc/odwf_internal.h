@@ -81,6 +81,8 @@ struct HopArgs {
     int g5;              // G5_* flags
     int Vh, Ns;
     int slot;            // result slot of NORM / RESID
+    int parity;          // output parity (bulk-staged kernels derive in-block neighbours from it)
+    unsigned int* fault; // set to 1 if a bulk-copy wait ran out of time (never expected)
 };
 
 // ---- host-side handle --------------------------------------------------------------------------
@@ -130,6 +132,8 @@ struct odwf_s {
     void* f64[4] = {nullptr, nullptr, nullptr, nullptr};
     // 4D scratch
     double* acc4 = nullptr;
+    unsigned int* fault = nullptr;        // device word, see HopArgs::fault
+    int staged = 0;                       // use the bulk-staged hop kernels where they apply (ODWF_STAGED=1)
     // batch-solve pools: per-system workspaces, solver states, reduction buffers, kernel arguments
     std::vector<odwf::Workspace> bws;
     odwf::CGState* bstate = nullptr;
@@ -183,6 +187,7 @@ int launch_axpy_to64(odwf_s* h, double a, const void* xin, int st_in, const floa
 int launch_norm2(odwf_s* h, const void* v, int storage, const float* scale, int slot, cudaStream_t st,
                  CGState* state = nullptr, double* partials = nullptr);
 void hop_fill(odwf_s* h, int storage, int parity, HopArgs& a, bool reduces);
+int launch_hop_own_cgb(odwf_s* h, int storage, HopArgs a, cudaStream_t st);
 int launch_hop_multi(odwf_s* h, int storage, bool mixhop, bool own, bool mixown, int epi, const HopArgs* dev_args,
                      int n, int max_vh, cudaStream_t st);
 int launch_gauge(odwf_s* h, const double* U, cudaStream_t st);

@@ -218,3 +218,17 @@ def test_solve_multi_uneven_lattices(lib):
     for op, b, x, (m1, m2) in zip(ops, bs, xs, m12):
         res = np.linalg.norm(b - op.ht(x.cpu().numpy(), m1, m2)) / np.linalg.norm(b)
         assert res <= 1.05e-10
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[2], CASES[3]])
+def test_staged_and_plain_kernels_agree(lib, case, monkeypatch):
+    """The bulk-staged FP32/FP16 hop kernels and the per-thread-gather kernels compute the same sums."""
+    dims, Ns = case[0], case[1]
+    psi = inputs.gaussian_spinor5(dims, Ns, 600)
+    outs = {}
+    for staged in ("0", "1"):
+        monkeypatch.setenv("ODWF_STAGED", staged)
+        lat, op, U, om = _setup(lib, *case)
+        outs[staged] = lat.apply(torch.from_numpy(psi).cuda(), 0.05, 0.5, op="dt", prec="single").cpu().numpy()
+        lat.close()
+    assert _rel(outs["1"], outs["0"]) < 1e-7
