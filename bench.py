@@ -89,6 +89,9 @@ class ClockSampler:
 # algorithmic bytes per launch of the fused hopping kernels (per 5D half-site: spinor reads and
 # writes of 24 reals, links 8 x 18 reals per 4D half-site shared by Ns slices)
 def alg_bytes(key, Vh, Ns):
+    if key >= 2000000:  # learned-preconditioner layer: cin inputs, cout outputs, optional own field, FP32
+        cin, cout, own = (key // 100) % 10, (key // 10) % 10, key % 10
+        return Vh * Ns * 96 * (cin + cout + own) + Vh * 8 * 18 * 4
     st = (key // 100000) % 10
     hop, mixhop, own, mixown, epi = (key // 10000) % 10, (key // 1000) % 10, (key // 100) % 10, (key // 10) % 10, key % 10
     rb = {0: 8, 1: 4, 2: 2}[st]        # bytes per real of the spinor storage
@@ -114,6 +117,8 @@ def alg_bytes(key, Vh, Ns):
 
 
 def kernel_name(key):
+    if key >= 2000000:
+        return f"k_net_layer<cin={(key // 100) % 10},cout={(key // 10) % 10}{',own' if key % 10 else ''}>"
     st = ["fp64", "fp32", "fp16"][(key // 100000) % 10]
     staged = "staged," if key >= 1000000 else ""
     hop, mixhop, own, mixown, epi = (key // 10000) % 10, (key // 1000) % 10, (key // 100) % 10, (key // 10) % 10, key % 10
@@ -181,6 +186,11 @@ def main():
     ap.add_argument("--delta", type=float, default=None,
                     help="reliable-update trigger of the inner solver (default 0.01 FP32, 0.1 FP16)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip the hot-path pass, batch and learned sections")
+    ap.add_argument("--no-tune", action="store_true", help="skip the launch autotuner")
+    ap.add_argument("--train-steps", type=int, default=40)
+    ap.add_argument("--method", default="learned", choices=["learned", "cgne"],
+                    help="timed solver: learned-preconditioned CGNE (default) or plain mixed-precision CGNE")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--ref-iters", type=int, default=1700)
     ap.add_argument("--dims", default=None, help="override lattice, e.g. 16,16,16,16 (profiling only)")
@@ -222,8 +232,36 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    tune_report = None
+    if not args.no_tune:
+        t0 = time.perf_counter()
+        tune_report = lat.autotune(args.prec)
+        tune_report = {"seconds": time.perf_counter() - t0,
+                       "chosen": [l for l in tune_report.splitlines() if l.startswith("chosen")]}
+    learned_setup = None
+    net = None
+    if args.method == "learned":
+        from paper_1710_09621_gb300.binding import Net
+        net = Net(lat, channels=2)
+        rs = [torch.from_numpy(inputs.gaussian_spinor5(DIMS, NS, inputs.seed_for(4, i))).to(dev) for i in range(4)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        net.set_pairs(rs, MASS, MASS, tol=1e-8)
+        t1 = time.perf_counter()
+        losses = net.train(args.train_steps, 2e-3)
+        t2 = time.perf_counter()
+        learned_setup = {"pairs": len(rs), "pair_seconds": t1 - t0, "train_steps": args.train_steps,
+                         "train_seconds": t2 - t1, "loss_first": float(losses[0]), "loss_last": float(losses[-1])}
+        del rs
+        lopts = solve_opts(tol=TOL, prec="single", delta=1e-3)
+
+        def do_solve(bb, xx=None):
+            return net.solve(bb, MASS, MASS, opts=lopts)
+    else:
+        def do_solve(bb, xx=None):
+            return lat.solve(bb, MASS, MASS, x=xx, opts=opts)
     for _ in range(args.warmup):
-        x, st = lat.solve(b, MASS, MASS, opts=opts)
+        x, st = do_solve(b)
     # ---- timed region: device-resident inputs -------------------------------------------------
     lat.profile(True)
     barrier()
@@ -232,7 +270,7 @@ def main():
     with ClockSampler(local) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
-            x, st = lat.solve(b, MASS, MASS, x=x, opts=opts)
+            x, st = do_solve(b, x)
             stats.append(st)
         ev1.record(stream)
         barrier()
@@ -252,7 +290,7 @@ def main():
     e0.record(stream)
     for _ in range(args.steps):
         bd = b_host.to(dev, non_blocking=True)
-        xd, _ = lat.solve(bd, MASS, MASS, opts=opts)
+        xd, _ = do_solve(bd)
         x_host.copy_(xd, non_blocking=True)
     e1.record(stream)
     barrier()
@@ -261,6 +299,20 @@ def main():
     if dist is not None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     e2e_value = float(t.item()) / (args.steps * world)
+
+    # ---- the other mixed-precision method on the same system ---------------------------------------
+    other = None
+    if args.method == "learned":
+        barrier()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(2):
+            _, stc = lat.solve(b, MASS, MASS, opts=opts)
+        c1.record(stream)
+        barrier()
+        other = {"method": f"CGNE, inner {args.prec}, FP64 reliable updates (no network)",
+                 "seconds": c0.elapsed_time(c1) / 2e3, "iters": stc["iters"],
+                 "true_residual": stc["true_residual"]}
 
     # ---- plain FP64 GPU CGNE on the same system ----------------------------------------------
     fp64 = None
@@ -272,6 +324,82 @@ def main():
         f1.record(stream)
         barrier()
         fp64 = {"seconds": f0.elapsed_time(f1) / 1e3, "iters": st64["iters"], "true_residual": st64["true_residual"]}
+
+    # ---- the rest of the hot path on the same lattice --------------------------------------------
+    extra = {}
+    if not args.quick:
+        from paper_1710_09621_gb300.binding import MP_NEW, Net, mp_terms
+
+        def timed(fn):
+            barrier()
+            t0 = time.perf_counter()
+            out = fn()
+            barrier()
+            return out, time.perf_counter() - t0
+
+        # one pass of the new-MP EOFA term list (heat-bath, action, force per term), Eq.(new_MP)
+        terms = mp_terms(MP_NEW, MASS, [0.1], 1.0)
+        eta = torch.from_numpy(inputs.gaussian_spinor(DIMS, inputs.seed_for(1, 200 + rank))).to(dev)
+        hp_opts = solve_opts(tol=TOL, prec=args.prec, delta=args.delta)
+
+        def hot_pass():
+            rec = []
+            for t in terms:
+                phi, hb = lat.heatbath(t, eta, opts=hp_opts)
+                S, st_a = lat.action(t, phi, opts=hp_opts)
+                F, st_f = lat.force(t, phi, opts=hp_opts)
+                rec.append({"chirality": t.chirality, "m3": t.m3, "m4": t.m4, "m_den": t.m_den,
+                            "poles": hb["n_poles"], "hb_iters": hb["iters"], "action": S,
+                            "action_iters": st_a["iters"], "force_iters": st_f["iters"],
+                            "force_magnitude": float(torch.sqrt((F ** 2).sum()).item() / (4 * F[0].numel() / 8))})
+            return rec
+        rec, t_hp = timed(hot_pass)
+        extra["hot_path_new_mp"] = {"seconds": t_hp, "terms": rec,
+                                    "what": "heat-bath (batched pole solves) + action + force for each term of "
+                                            "(m,m)/(M,M) = (m,m)/(m,mh) (m,mh)/(M,mh) (M,mh)/(M,M), m=0.01, mh=0.1, M=1"}
+        # batch of 4 systems with different masses vs one after another
+        m12 = [(MASS, MASS), (MASS, 0.1), (1.0, 0.1), (0.1, 0.1)]
+        bsb = [torch.from_numpy(inputs.gaussian_spinor5(DIMS, NS, inputs.seed_for(1, 300 + i))).to(dev) for i in range(4)]
+        _, t_batch = timed(lambda: lat.solve_batch(bsb, m12, opts=opts))
+        _, t_seq = timed(lambda: [lat.solve(b_, *mm, opts=opts) for b_, mm in zip(bsb, m12)])
+        extra["batch4"] = {"seconds_batched": t_batch, "seconds_sequential": t_seq, "masses": m12}
+        # uneven batch: 8^4, 12^4 and the 16^3 x 32 lattice (Ns = 16) advancing in one launch per step
+        from paper_1710_09621_gb300.binding import ODWF as _ODWF, solve_multi
+        lats_u, bs_u = [], []
+        for k, dd in enumerate([(8, 8, 8, 8), (12, 12, 12, 12)]):
+            lu = _ODWF(dd, NS, M0, om)
+            lu.set_gauge(torch.from_numpy(inputs.random_su3_links(dd, EPS, inputs.seed_for(3, k))).to(dev))
+            lats_u.append(lu)
+            bs_u.append(torch.from_numpy(inputs.gaussian_spinor5(dd, NS, inputs.seed_for(3, 10 + k))).to(dev))
+        lats_u.append(lat)
+        bs_u.append(b)
+        mu = [(MASS, MASS)] * 3
+        (_, stu), t_unb = timed(lambda: solve_multi(lats_u, bs_u, mu, opts=opts))
+        _, t_uns = timed(lambda: [lz.solve(bz, MASS, MASS, opts=opts) for lz, bz in zip(lats_u, bs_u)])
+        extra["uneven_batch"] = {"lattices": ["8^4", "12^4", "16^3x32"], "Ns": NS,
+                                 "seconds_one_launch_per_step": t_unb, "seconds_sequential": t_uns,
+                                 "iters": [s_["iters"] for s_ in stu]}
+        for lz in lats_u[:2]:
+            lz.close()
+    if not args.quick:
+        # preconditioned solve with the untrained (Neumann-series) network, and, when the timed method
+        # is plain CGNE, with a trained one
+        neu = Net(lat, channels=2)
+        (xn, stn), t_n = timed(lambda: neu.solve(b, MASS, MASS, opts=solve_opts(tol=TOL, prec="single", delta=1e-3)))
+        extra["neumann_network_solve"] = {"seconds": t_n, "iters": stn["iters"], "true_residual": stn["true_residual"]}
+        neu.close()
+    if not args.quick and args.method == "cgne":
+        # learned preconditioner: pairs from the solver, Adam, then preconditioned solves
+        net = Net(lat, channels=2)
+        rs = [torch.from_numpy(inputs.gaussian_spinor5(DIMS, NS, inputs.seed_for(4, i))).to(dev) for i in range(4)]
+        _, t_pairs = timed(lambda: net.set_pairs(rs, MASS, MASS, tol=1e-8))
+        losses, t_train = timed(lambda: net.train(args.train_steps, 2e-3))
+        lopts = solve_opts(tol=TOL, prec="single", delta=1e-3)
+        (xl, stl), t_l = timed(lambda: net.solve(b, MASS, MASS, opts=lopts))
+        extra["learned"] = {"pairs": len(rs), "pair_seconds": t_pairs, "train_steps": args.train_steps,
+                            "train_seconds": t_train, "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
+                            "trained": {"seconds": t_l, "iters": stl["iters"], "true_residual": stl["true_residual"]}}
+        net.close()
 
     # ---- roofline of the dominant kernel -------------------------------------------------------
     Vh = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] // 2
@@ -297,8 +425,9 @@ def main():
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"single": "f32 (FP64 reliable updates)", "half": "f16 storage/f32 (FP64 reliable updates)",
-                  "double": "f64"}[args.prec],
+        "dtype": ("f32 + bf16 tensor-core network (FP64 residual restarts)" if args.method == "learned" else
+                  {"single": "f32 (FP64 reliable updates)", "half": "f16 storage/f32 (FP64 reliable updates)",
+                   "double": "f64"}[args.prec]),
         "data": "synthetic",
         "config": dict(WORKLOAD, prec=args.prec, delta=args.delta, l2="inputs larger than L2 (each solve streams >1 GB)",
                        parallelism=f"replicas x{world}"),
@@ -312,7 +441,14 @@ def main():
                 "d2h_bytes_per_step": x_host.numel() * 16},
         "gpu_launches": int(sum(k["launches"] for k in kern)),
         "clocks": clk.summary(),
+        "autotune": tune_report,
+        "method": {"learned": "CGNE on S M with the trained gauge-equivariant network M (BF16 tensor-core "
+                              "channel mixing), FP32 inner cycles restarted from the FP64 residual",
+                   "cgne": f"CGNE, inner {args.prec}, FP64 reliable updates"}[args.method],
+        "learned_setup": learned_setup,
+        "cgne_same_run": other,
     }
+    line.update(extra)
     if rank == 0 and not args.no_cpu and world == 1:
         n_it = fp64["iters"] if fp64 else args.ref_iters
         s = cpu_oracle_sample(n_it)

@@ -190,6 +190,13 @@ int odwf_net_train(odwf_net_t* net, int steps, double lr, double* losses, void* 
 int eofa_solve_learned(odwf_t* h, odwf_net_t* net, double m1, double m2, const void* b, void* x,
                        const odwf_solve_opts* opts, odwf_solve_stats* stats, void* stream);
 
+/* Autotuner: times the launch choices (grid size: one resident wave, one CTA per site group, two or
+ * four waves; per-thread neighbour gathers or bulk-staged gathers) of the four fused kernels of the
+ * CGNE iteration in precision prec on this handle's lattice and keeps the fastest for later calls.
+ * report (may be NULL) receives the timings as text. Overwrites the handle's inner work fields and
+ * solver state; call it between solves. */
+int odwf_autotune(odwf_t* h, int prec, char* report, int report_len, void* stream);
+
 /* Kernel timing for measurement: while enabled, every launch of the fused hopping kernels is
  * bracketed by CUDA events on its stream. odwf_profile_read synchronises the device and returns,
  * per kernel variant seen since the last enable, its key (storage*100000 + hop*10000 +

@@ -31,7 +31,7 @@ EXPORTS = ["odwf_create", "odwf_destroy", "odwf_last_error", "odwf_set_gauge", "
            "odwf_omega_vector", "odwf_profile_enable", "odwf_profile_read", "eofa_mp_terms",
            "odwf_apply_noalloc", "eofa_solve_multi", "odwf_net_create", "odwf_net_destroy",
            "odwf_net_num_params", "odwf_net_weights", "odwf_net_apply", "odwf_net_set_pairs", "odwf_net_loss_grad",
-           "odwf_net_train", "eofa_solve_learned"]
+           "odwf_net_train", "eofa_solve_learned", "odwf_autotune"]
 
 
 class OdwfError(RuntimeError):
@@ -98,6 +98,7 @@ def load_library(path: str = LIB_PATH):
     lib.odwf_profile_read.argtypes = [vp, ip, ip, dp, ip]
     lib.eofa_mp_terms.argtypes = [i, d, dp, i, d, i, ctypes.POINTER(Term), i, ip]
     lib.odwf_apply_noalloc.argtypes = [vp, i, d, d, vp, vp, i, vp]
+    lib.odwf_autotune.argtypes = [vp, i, ctypes.c_char_p, i, vp]
     lib.odwf_net_create.argtypes = [vp, i, ctypes.POINTER(vp)]
     lib.odwf_net_destroy.argtypes = [vp]
     lib.odwf_net_num_params.argtypes = [vp]
@@ -258,6 +259,12 @@ class ODWF:
         self._check(self.lib.eofa_heatbath(self.h, ctypes.byref(t), _ptr(eta), _ptr(phi), ctypes.byref(hb),
                                            _stream_ptr(stream)))
         return phi, {"n_poles": hb.n_poles_out, "iters": hb.iters_out}
+
+    def autotune(self, prec="single", stream=None):
+        """Pick the fastest launch choice of each fused CGNE kernel; returns the timing report."""
+        buf = ctypes.create_string_buffer(8192)
+        self._check(self.lib.odwf_autotune(self.h, _PREC[prec], buf, 8192, _stream_ptr(stream)))
+        return buf.value.decode()
 
     def profile(self, enable=True):
         self._check(self.lib.odwf_profile_enable(self.h, 1 if enable else 0))

@@ -591,3 +591,34 @@ extern "C" int eofa_mp_terms(int scheme, double m, const double* mh, int n_mh, d
     *n_out = n;
     return ODWF_OK;
 }
+
+// ---- autotuning --------------------------------------------------------------------------------
+namespace odwf {
+int autotune_storage(odwf_s* h, int stg, const SCoef* c, cudaStream_t st, std::vector<std::string>& log);
+}
+
+extern "C" int odwf_autotune(odwf_t* h, int prec, char* report, int report_len, void* stream) {
+    if (!h) return ODWF_EINVAL;
+    if (prec != ODWF_PREC_DOUBLE && prec != ODWF_PREC_SINGLE && prec != ODWF_PREC_HALF)
+        return set_err(h, ODWF_EINVAL, "autotune: bad precision");
+    const int stg = prec == ODWF_PREC_DOUBLE ? ST_DOUBLE : (prec == ODWF_PREC_SINGLE ? ST_FLOAT : ST_HALF);
+    int rc = ensure_workspace(h, stg);
+    if (rc) return rc;
+    const SCoef* c = get_coef(h, 0.5, 0.5);
+    if (!c) return ODWF_EINVAL;
+    std::vector<std::string> log;
+    rc = autotune_storage(h, stg, c, (cudaStream_t)stream, log);
+    if (report && report_len > 0) {
+        std::string all;
+        for (auto& l : log) all += l + "\n";
+        for (auto& kv : h->tune) {
+            char buf[96];
+            std::snprintf(buf, sizeof buf, "chosen key %d: grid-mode %d staged %d\n", kv.first, kv.second.first,
+                          kv.second.second);
+            all += buf;
+        }
+        std::strncpy(report, all.c_str(), report_len - 1);
+        report[report_len - 1] = 0;
+    }
+    return rc;
+}

@@ -19,6 +19,8 @@ namespace odwf {
 int ensure_workspace(odwf_s* h, int inner);
 int solve_core(odwf_s* h, double m1, double m2, const odwf_solve_opts* opts, odwf_solve_stats* stats,
                cudaStream_t st);
+int solve_shared_rhs(odwf_s* h, int n, const double* m12, const void* be, const void* bo, const odwf_solve_opts* opts,
+                     odwf_solve_stats* stats, std::vector<Workspace*>& ws_out, cudaStream_t st);
 
 struct SWeights {
     double w[kMaxNs];
@@ -307,12 +309,14 @@ static int embed(odwf_s* h, const eofa_term* t, const void* phi, cudaStream_t st
     return cuda_check(h, cudaGetLastError(), "k_embed");
 }
 
-static int contract(odwf_s* h, int chir, const double* w, const void* phi, void* out4, int slot, cudaStream_t st) {
+static int contract(odwf_s* h, int chir, const double* w, const void* phi, void* out4, int slot, cudaStream_t st,
+                    const Workspace* ws = nullptr) {
+    if (!ws) ws = &h->ws;
     SWeights c{};
     for (int s = 0; s < h->Ns; ++s) c.w[s] = w[s];
     int g = grid_for(h, (size_t)2 * h->Vh, 256);
     if (2 * g > h->partials_n) g = h->partials_n / 2;
-    k_contract<<<g, 256, 0, st>>>((const double*)h->ws.x_e, (const double*)h->ws.x_o, h->lexof[0], h->lexof[1], h->Vh,
+    k_contract<<<g, 256, 0, st>>>((const double*)ws->x_e, (const double*)ws->x_o, h->lexof[0], h->lexof[1], h->Vh,
                                   h->Ns, chir, c, (const double2*)phi, (double2*)out4, h->state, h->partials, slot);
     return cuda_check(h, cudaGetLastError(), "k_contract");
 }
@@ -491,21 +495,26 @@ extern "C" int eofa_heatbath(odwf_t* h, const eofa_term* t, const void* eta, voi
     if ((rc = embed(h, t, eta, st))) return rc;
     double om[kMaxNs];
     omega_vec(h, t->chirality, om);
-    int iters = 0;
-    int worst = ODWF_OK;
+    // every pole is one shifted-mass system with the same source: solve them as one batch
+    std::vector<double> m12(2 * (size_t)n), wl(n);
     for (int l = 0; l < n; ++l) {
         const double kp = k / (1.0 + r.b[l]);
         const double mp = (kp * (1.0 + mref) + 2.0 * mref) / (2.0 - kp * (1.0 + mref));
-        odwf_solve_stats ss{};
-        const int src = t->chirality < 0 ? solve_core(h, t->m3, mp, &so, &ss, st)
-                                         : solve_core(h, mp, t->m4, &so, &ss, st);
-        if (src != ODWF_OK && src != ODWF_ENOCONV) return src;
-        if (src != ODWF_OK) worst = src;
-        iters += ss.iters;
-        const double wl = (t->chirality < 0 ? 1.0 : -1.0) * (r.a[l] / (1.0 + r.b[l])) * kp;
+        m12[2 * l] = t->chirality < 0 ? t->m3 : mp;
+        m12[2 * l + 1] = t->chirality < 0 ? mp : t->m4;
+        wl[l] = (t->chirality < 0 ? 1.0 : -1.0) * (r.a[l] / (1.0 + r.b[l])) * kp;
+    }
+    std::vector<odwf_solve_stats> ss(n);
+    std::vector<Workspace*> wsx;
+    const int src = solve_shared_rhs(h, n, m12.data(), h->ws.b_e, h->ws.b_o, &so, ss.data(), wsx, st);
+    if (src != ODWF_OK && src != ODWF_ENOCONV) return src;
+    const int worst = src;
+    int iters = 0;
+    for (int l = 0; l < n; ++l) {
+        iters += ss[l].iters;
         double w[kMaxNs];
-        for (int s = 0; s < h->Ns; ++s) w[s] = wl * om[s];
-        if ((rc = contract(h, t->chirality, w, nullptr, phi, 0, st))) return rc;
+        for (int q = 0; q < h->Ns; ++q) w[q] = wl[l] * om[q];
+        if ((rc = contract(h, t->chirality, w, nullptr, phi, 0, st, wsx[l]))) return rc;
     }
     if (hb) {
         hb->n_poles_out = n;

@@ -365,6 +365,18 @@ __device__ __forceinline__ void hop_body(const HopArgs& a) {
     if (REDUCE) grid_finalize<EPI>(a, part);
 }
 
+// The system's arguments are copied once into shared memory, so field accesses in the body are
+// shared-memory broadcasts rather than repeated global loads.
+__device__ __forceinline__ const HopArgs& stage_args(const HopArgs* __restrict__ args, HopArgs* sa) {
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    constexpr int nw = (int)(sizeof(HopArgs) / sizeof(int));
+    const int* src = reinterpret_cast<const int*>(args + blockIdx.y);
+    int* dst = reinterpret_cast<int*>(sa);
+    for (int i = tid; i < nw; i += blockDim.x * blockDim.y) dst[i] = __ldg(src + i);
+    __syncthreads();
+    return *sa;
+}
+
 // ---- bulk-staged variant ------------------------------------------------------------------------
 // The same operator as hop_body, but the CTA first requests all the neighbour spinors it needs
 // with asynchronous bulk copies (cp.async.bulk, completion on one shared-memory mbarrier), so the
@@ -646,7 +658,8 @@ __global__ void __launch_bounds__(256) k_hop_staged(HopArgs a) {
 
 template <int ST, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
 __global__ void __launch_bounds__(256) k_hop_staged_multi(const HopArgs* __restrict__ args) {
-    hop_body_staged<ST, MIXHOP, OWN, MIXOWN, EPI>(args[blockIdx.y]);
+    __shared__ HopArgs sa;
+    hop_body_staged<ST, MIXHOP, OWN, MIXOWN, EPI>(stage_args(args, &sa));
 }
 
 template <int ST>
@@ -666,7 +679,8 @@ __global__ void __launch_bounds__(256) k_hop(HopArgs a) {
 // Systems that are converged or waiting for a host-side update return at once.
 template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
 __global__ void __launch_bounds__(256) k_hop_multi(const HopArgs* __restrict__ args) {
-    hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(args[blockIdx.y]);
+    __shared__ HopArgs sa;
+    hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(stage_args(args, &sa));
 }
 
 // ---- launch ------------------------------------------------------------------------------------
@@ -696,11 +710,28 @@ void hop_fill(odwf_s* h, int storage, int parity, HopArgs& a, bool reduces) {
 
 // The bulk-staged kernels need CTAs of whole 2^4 blocks (spb a multiple of 8) and, for FP16,
 // 16-byte scale rows (Ns a multiple of 4).
-static bool staged_ok(const odwf_s* h, int st) {
-    if (!h->staged || st == ST_DOUBLE) return false;
+static bool staged_geom_ok(const odwf_s* h, int st) {
+    if (st == ST_DOUBLE) return false;
     if (spb_for(h->Ns) % 8) return false;
     if (st == ST_HALF && h->Ns % 4) return false;
     return true;
+}
+
+static bool staged_ok(const odwf_s* h, int st) { return h->staged && staged_geom_ok(h, st); }
+
+// Grid of a fused kernel: mode 0 one resident wave (SMs x occupancy), 1 one CTA per site group,
+// 2 / 3 two / four resident waves; reducing kernels are capped by the partial-sum buffer.
+static int grid_for_mode(const odwf_s* h, int mode, int occ, int groups, bool reduces) {
+    long g;
+    switch (mode) {
+        case 1: g = groups; break;
+        case 2: g = 2L * h->num_sms * occ; break;
+        case 3: g = 4L * h->num_sms * occ; break;
+        default: g = (long)h->num_sms * occ; break;
+    }
+    if (g > groups) g = groups;
+    if (reduces && g > h->partials_n) g = h->partials_n;
+    return g < 1 ? 1 : (int)g;
 }
 
 template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
@@ -769,15 +800,19 @@ template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
 static int launch_one(odwf_s* h, int parity, HopArgs a, cudaStream_t st) {
     const int Ns = h->Ns, spb = spb_for(Ns);
     size_t smem = 0;
-    const bool stg = KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::CAN_STAGE && staged_ok(h, ST);
+    const int base_key = ST * 100000 + HOP * 10000 + MIXHOP * 1000 + OWN * 100 + MIXOWN * 10 + EPI;
+    bool stg = KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::CAN_STAGE && staged_ok(h, ST);
+    int mode = 0;
+    auto tuned = h->tune.find(base_key);
+    if (tuned != h->tune.end()) {
+        mode = tuned->second.first;
+        stg = KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::CAN_STAGE && staged_geom_ok(h, ST) && tuned->second.second;
+    }
     const int occ = occupancy<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(h, stg ? 2 : 0, &smem);
     const int groups = (h->Vh + spb - 1) / spb;
-    int grid = h->num_sms * occ;
-    if (grid > groups) grid = groups;
-    if (grid < 1) grid = 1;
-    if (EPI != EPI_STORE && grid > h->partials_n) return set_err(h, ODWF_EINVAL, "partials buffer too small");
+    const int grid = grid_for_mode(h, mode, occ, groups, EPI != EPI_STORE);
     hop_fill(h, ST, parity, a, EPI != EPI_STORE);
-    const int key = (stg ? 1000000 : 0) + ST * 100000 + HOP * 10000 + MIXHOP * 1000 + OWN * 100 + MIXOWN * 10 + EPI;
+    const int key = (stg ? 1000000 : 0) + base_key;
     cudaEvent_t ev0 = nullptr;
     if (h->prof) prof_begin(h, key, st, &ev0);
     if constexpr (KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::CAN_STAGE) {
@@ -1112,4 +1147,106 @@ int launch_gauge(odwf_s* h, const double* U, cudaStream_t st) {
     return cuda_check(h, cudaGetLastError(), "k_gauge");
 }
 
+
+// ---- autotuner ------------------------------------------------------------------------------------
+// Times every launch choice (grid mode 0..3, bulk-staged or per-thread gather) of the four fused
+// kernels of the CGNE iteration in one storage precision, on the handle's own lattice, and keeps
+// the fastest per kernel. Inputs are the inner work fields filled with a constant byte pattern
+// (finite, positive values), and a private solver state that never stops the kernels.
+int autotune_storage(odwf_s* h, int stg, const SCoef* c, cudaStream_t st, std::vector<std::string>& log) {
+    Workspace& w = h->ws;
+    const size_t bi = half_elems_bytes(h, stg == ST_HALF ? ST_FLOAT : stg);
+    const size_t bs = sizeof(float) * (size_t)h->Vh * h->Ns;
+    void* fields[4] = {w.xi, w.ri, w.pi, w.ti};
+    float* scales[4] = {w.xi_s, w.ri_s, w.pi_s, w.ti_s};
+    auto fill = [&]() -> int {
+        for (int i = 0; i < 4; ++i) {
+            if (cudaMemsetAsync(fields[i], 0x3c, bi, st) != cudaSuccess) return ODWF_ECUDA;
+            if (stg == ST_HALF && cudaMemsetAsync(scales[i], 0x3c, bs, st) != cudaSuccess) return ODWF_ECUDA;
+        }
+        CGState hs{};
+        hs.rr = 1.0;
+        hs.pp = 1.0;
+        hs.alpha = 0.01;
+        hs.beta = 0.5;
+        hs.tol2 = -1.0;
+        hs.rr_max = 1.0;
+        hs.maxiter = 1 << 30;
+        if (cudaMemcpyAsync(h->state, &hs, sizeof(CGState), cudaMemcpyHostToDevice, st) != cudaSuccess) return ODWF_ECUDA;
+        return cudaStreamSynchronize(st) == cudaSuccess ? ODWF_OK : ODWF_ECUDA;
+    };
+    const int NN = h->Ns * h->Ns;
+    struct V {
+        const char* name;
+        bool mixhop, own, mixown;
+        int epi, parity;
+    } vars[4] = {{"K1", true, false, false, EPI_STORE, 1},
+                 {"K2A", false, true, true, EPI_CG_A, 0},
+                 {"K2B", false, true, true, EPI_CG_B, 0},
+                 {"K2", false, true, true, EPI_STORE, 0}};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const bool can_stage = staged_geom_ok(h, stg);
+    const int saved_prof = h->prof;
+    h->prof = false;
+    for (const V& v : vars) {
+        const int base_key = stg * 100000 + 1 * 10000 + v.mixhop * 1000 + v.own * 100 + v.mixown * 10 + v.epi;
+        HopArgs a{};
+        a.in = w.ti;
+        a.in_scale = w.ti_s;
+        a.own = w.pi;
+        a.own_scale = w.pi_s;
+        a.out = v.epi == EPI_STORE ? w.ti : nullptr;
+        a.out_scale = w.ti_s;
+        if (v.mixhop) {
+            a.in = w.pi;
+            a.in_scale = w.pi_s;
+        }
+        a.mhop = c->dev + (size_t)2 * NN;
+        a.mown = c->dev;
+        a.c_hop = v.mixhop ? 1.0 : -0.25;
+        a.x = w.xi;
+        a.x_scale = w.xi_s;
+        a.r = v.epi == EPI_CG_B ? w.pi : w.ri;
+        a.r_scale = v.epi == EPI_CG_B ? w.pi_s : w.ri_s;
+        if (v.epi == EPI_STORE && !v.mixhop) {
+            a.out = w.ri;  // plain store variant writes r (a throw-away field here)
+            a.out_scale = w.ri_s;
+        }
+        a.state = (v.epi == EPI_STORE) ? nullptr : h->state;
+        float best = 1e30f;
+        std::pair<int, int> best_choice{0, 0};
+        for (int staged = 0; staged <= (can_stage ? 1 : 0); ++staged)
+            for (int mode = 0; mode < 4; ++mode) {
+                h->tune[base_key] = {mode, staged};
+                int rc = fill();
+                if (rc) return set_err(h, rc, "autotune: fill");
+                for (int k = 0; k < 2; ++k)
+                    if ((rc = launch_hop(h, stg, v.parity, v.mixhop, v.own, v.mixown, v.epi, a, st))) return rc;
+                cudaEventRecord(e0, st);
+                const int reps = 10;
+                for (int k = 0; k < reps; ++k)
+                    if ((rc = launch_hop(h, stg, v.parity, v.mixhop, v.own, v.mixown, v.epi, a, st))) return rc;
+                cudaEventRecord(e1, st);
+                if ((rc = cuda_check(h, cudaEventSynchronize(e1), "autotune sync"))) return rc;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms /= reps;
+                char buf[160];
+                std::snprintf(buf, sizeof buf, "%s storage %d staged %d grid-mode %d: %.1f us", v.name, stg, staged, mode,
+                              1e3 * ms);
+                log.push_back(buf);
+                if (ms < best) {
+                    best = ms;
+                    best_choice = {mode, staged};
+                }
+            }
+        h->tune[base_key] = best_choice;
+    }
+    h->prof = saved_prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ODWF_OK;
+}
 }  // namespace odwf

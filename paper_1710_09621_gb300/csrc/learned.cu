@@ -538,7 +538,11 @@ int net_layer(odwf_net_s* n, int parity, int cin, int cout, const float* const* 
         }
         int occ = 1;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, h->Ns * spb, smem);
+        const int key = 2000000 + cin * 100 + cout * 10 + (own ? 1 : 0);
+        cudaEvent_t ev0 = nullptr;
+        if (h->prof) prof_begin(h, key, st, &ev0);
         fn<<<grid_for_groups(h, occ < 1 ? 1 : occ), blk, smem, st>>>(a);
+        if (h->prof) prof_end(h, key, st, ev0);
         return cuda_check(h, cudaGetLastError(), "k_net_layer");
     };
     if (cin == 1 && cout == 2) return launch(k_net_layer<1, 2>);

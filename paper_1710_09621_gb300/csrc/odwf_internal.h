@@ -134,6 +134,8 @@ struct odwf_s {
     double* acc4 = nullptr;
     unsigned int* fault = nullptr;        // device word, see HopArgs::fault
     int staged = 0;                       // use the bulk-staged hop kernels where they apply (ODWF_STAGED=1)
+    // autotuned launch choice per kernel variant (key without the staged flag): grid mode, staged
+    std::map<int, std::pair<int, int>> tune;
     // batch-solve pools: per-system workspaces, solver states, reduction buffers, kernel arguments
     std::vector<odwf::Workspace> bws;
     odwf::CGState* bstate = nullptr;

@@ -567,6 +567,34 @@ int solve_multi(odwf_s* const* hs, int n, const double* m12, const void* const* 
     return src;
 }
 
+// n systems on handle h sharing one right-hand side b' given in the internal FP64 layout (be, bo):
+// D_T(m12[2i], m12[2i+1]) x_i = b'. On return ws_out[i] holds x_i in x_e / x_o.
+int solve_shared_rhs(odwf_s* h, int n, const double* m12, const void* be, const void* bo, const odwf_solve_opts* opts,
+                     odwf_solve_stats* stats, std::vector<Workspace*>& ws_out, cudaStream_t st) {
+    int rc = ensure_batch(h, n);
+    if (rc) return rc;
+    std::vector<Slot> S(n);
+    const size_t b64 = half_elems_bytes(h, ST_DOUBLE);
+    ws_out.assign(n, nullptr);
+    for (int i = 0; i < n; ++i) {
+        S[i].h = h;
+        S[i].m1 = m12[2 * i];
+        S[i].m2 = m12[2 * i + 1];
+        S[i].ws = &h->bws[i];
+        S[i].state = h->bstate + i;
+        S[i].hstate = h->bstate_host + i;
+        S[i].partials = h->bpartials + (size_t)i * h->partials_n;
+        if ((rc = ensure_ws(h, *S[i].ws, ST_DOUBLE))) return rc;
+        if ((rc = cuda_check(h, cudaMemcpyAsync(S[i].ws->b_e, be, b64, cudaMemcpyDeviceToDevice, st), "copy"))) return rc;
+        if ((rc = cuda_check(h, cudaMemcpyAsync(S[i].ws->b_o, bo, b64, cudaMemcpyDeviceToDevice, st), "copy"))) return rc;
+        ws_out[i] = S[i].ws;
+    }
+    const int src = solve_slots(S, opts, st);
+    for (int i = 0; i < n; ++i)
+        if (stats) stats[i] = S[i].stats;
+    return src;
+}
+
 }  // namespace odwf
 
 extern "C" int eofa_solve(odwf_t* h, double m1, double m2, const void* b, void* x, const odwf_solve_opts* opts,
