@@ -34,6 +34,20 @@ WORKLOAD = {"workload": "16^3x32 Ns=16 optimal DWF (Zolotarev omega on [0.05,6.2
 DIMS, NS, M0, MASS, EPS, TOL = (16, 16, 16, 32), 16, 1.3, 0.01, 0.3, 1e-10
 
 
+def reduce_max(value, dist=None, device="cpu"):
+    """Max of a per-rank float over all ranks (the slowest replica sets the job's time)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def per_solve_seconds(max_elapsed, steps, world):
+    """Whole-job seconds per solve: every rank solves `steps` systems in `max_elapsed` seconds."""
+    return max_elapsed / (steps * world)
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -276,12 +290,8 @@ def main():
         barrier()
     prof = lat.profile_read()
     lat.profile(False)
-    elapsed = ev0.elapsed_time(ev1) / 1e3
-    t = torch.tensor([elapsed], device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed = float(t.item())
-    value = elapsed / (args.steps * world)
+    elapsed = reduce_max(ev0.elapsed_time(ev1) / 1e3, dist, dev)
+    value = per_solve_seconds(elapsed, args.steps, world)
 
     # ---- e2e: pinned host input -> device -> solve -> pinned host output ------------------------
     x_host = torch.empty_like(b_host).pin_memory()
@@ -294,11 +304,7 @@ def main():
         x_host.copy_(xd, non_blocking=True)
     e1.record(stream)
     barrier()
-    e2e_el = e0.elapsed_time(e1) / 1e3
-    t = torch.tensor([e2e_el], device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = float(t.item()) / (args.steps * world)
+    e2e_value = per_solve_seconds(reduce_max(e0.elapsed_time(e1) / 1e3, dist, dev), args.steps, world)
 
     # ---- the other mixed-precision method on the same system ---------------------------------------
     other = None
