@@ -103,6 +103,10 @@ class ClockSampler:
 # algorithmic bytes per launch of the fused hopping kernels (per 5D half-site: spinor reads and
 # writes of 24 reals, links 8 x 18 reals per 4D half-site shared by Ns slices)
 def alg_bytes(key, Vh, Ns):
+    if key >= 3000000:  # GCR step kernels (FP32 half fields of Vh Ns 96 bytes)
+        kind, k = (key // 100) % 10, key % 100
+        fld = Vh * Ns * 96
+        return {1: (k + 2) * fld, 2: 0, 3: (2 * k + 8) * fld}[kind]
     if key >= 2000000:  # learned-preconditioner layer: cin inputs, cout outputs, optional own field, FP32
         cin, cout, own = (key // 100) % 10, (key // 10) % 10, key % 10
         return Vh * Ns * 96 * (cin + cout + own) + Vh * 8 * 18 * 4
@@ -131,6 +135,9 @@ def alg_bytes(key, Vh, Ns):
 
 
 def kernel_name(key):
+    if key >= 3000000:
+        kind, k = (key // 100) % 10, key % 100
+        return {1: f"k_gcr_dots<{k}>", 2: "k_gcr_sum", 3: f"k_gcr_update<{k}>"}[kind]
     if key >= 2000000:
         return f"k_net_layer<cin={(key // 100) % 10},cout={(key // 10) % 10}{',own' if key % 10 else ''}>"
     st = ["fp64", "fp32", "fp16"][(key // 100000) % 10]
@@ -193,7 +200,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="single", choices=["single", "half", "double"])
@@ -203,8 +210,13 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the hot-path pass, batch and learned sections")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch autotuner")
     ap.add_argument("--train-steps", type=int, default=40)
-    ap.add_argument("--method", default="learned", choices=["learned", "cgne"],
-                    help="timed solver: learned-preconditioned CGNE (default) or plain mixed-precision CGNE")
+    ap.add_argument("--method", default="learned", choices=["learned", "gcr", "cgne"],
+                    help="timed solver: learned-preconditioned CGNE (default), flexible GCR right-preconditioned "
+                         "by the learned network, or plain mixed-precision CGNE")
+    ap.add_argument("--nvec", type=int, default=8, help="GCR basis size")
+    ap.add_argument("--truncate", action="store_true", help="GCR keeps a sliding window of directions")
+    ap.add_argument("--gcr-sweep", action="store_true",
+                    help="also run flexible GCR (network / none, restarted / window) with an iteration cap")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--ref-iters", type=int, default=1700)
     ap.add_argument("--dims", default=None, help="override lattice, e.g. 16,16,16,16 (profiling only)")
@@ -254,7 +266,7 @@ def main():
                        "chosen": [l for l in tune_report.splitlines() if l.startswith("chosen")]}
     learned_setup = None
     net = None
-    if args.method == "learned":
+    if args.method in ("learned", "gcr"):
         from paper_1710_09621_gb300.binding import Net
         net = Net(lat, channels=2)
         rs = [torch.from_numpy(inputs.gaussian_spinor5(DIMS, NS, inputs.seed_for(4, i))).to(dev) for i in range(4)]
@@ -269,8 +281,12 @@ def main():
         del rs
         lopts = solve_opts(tol=TOL, prec="single", delta=1e-3)
 
-        def do_solve(bb, xx=None):
-            return net.solve(bb, MASS, MASS, opts=lopts)
+        if args.method == "learned":
+            def do_solve(bb, xx=None):
+                return net.solve(bb, MASS, MASS, opts=lopts)
+        else:
+            def do_solve(bb, xx=None):
+                return lat.solve_gcr(bb, MASS, MASS, net=net, nvec=args.nvec, truncate=args.truncate, opts=lopts)
     else:
         def do_solve(bb, xx=None):
             return lat.solve(bb, MASS, MASS, x=xx, opts=opts)
@@ -279,17 +295,19 @@ def main():
     # ---- timed region: device-resident inputs -------------------------------------------------
     lat.profile(True)
     barrier()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev0, ev1 = evs[0], evs[-1]
     stats = []
     with ClockSampler(local) as clk:
         ev0.record(stream)
-        for _ in range(args.steps):
+        for i in range(args.steps):
             x, st = do_solve(b, x)
             stats.append(st)
-        ev1.record(stream)
+            evs[i + 1].record(stream)
         barrier()
     prof = lat.profile_read()
     lat.profile(False)
+    step_s = [evs[i].elapsed_time(evs[i + 1]) / 1e3 for i in range(args.steps)]
     elapsed = reduce_max(ev0.elapsed_time(ev1) / 1e3, dist, dev)
     value = per_solve_seconds(elapsed, args.steps, world)
 
@@ -308,7 +326,7 @@ def main():
 
     # ---- the other mixed-precision method on the same system ---------------------------------------
     other = None
-    if args.method == "learned":
+    if args.method != "cgne":
         barrier()
         c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         c0.record(stream)
@@ -393,7 +411,29 @@ def main():
         neu = Net(lat, channels=2)
         (xn, stn), t_n = timed(lambda: neu.solve(b, MASS, MASS, opts=solve_opts(tol=TOL, prec="single", delta=1e-3)))
         extra["neumann_network_solve"] = {"seconds": t_n, "iters": stn["iters"], "true_residual": stn["true_residual"]}
+        if args.method == "gcr":
+            (_, stp), t_p = timed(lambda: net.solve(b, MASS, MASS, opts=solve_opts(tol=TOL, prec="single", delta=1e-3)))
+            extra["learned_pcgne"] = {"seconds": t_p, "iters": stp["iters"], "true_residual": stp["true_residual"]}
         neu.close()
+    if args.gcr_sweep:
+        # flexible GCR on S (right-preconditioned by the network, and without it); a run that ends above
+        # the tolerance within its iteration / time cap is reported with its final true residual
+        from paper_1710_09621_gb300.binding import Net
+        gnet = net if net is not None else Net(lat, channels=2)
+        gl = solve_opts(tol=TOL, prec="single", delta=1e-3, maxiter=3000, max_seconds=15.0)
+        gcr = {"sweep": [], "weights": "trained" if net is not None else "Neumann"}
+        for nv_, tr_ in ((8, False), (16, False), (4, True), (8, True)):
+            (_, stg), t_g = timed(lambda: lat.solve_gcr(b, MASS, MASS, net=gnet, nvec=nv_, truncate=tr_, opts=gl,
+                                                       allow_noconv=True))
+            gcr["sweep"].append({"nvec": nv_, "basis": "window" if tr_ else "restarted", "seconds": t_g,
+                                 "iters": stg["iters"], "true_residual": stg["true_residual"], "status": stg["status"]})
+        (_, stg0), t_g0 = timed(lambda: lat.solve_gcr(b, MASS, MASS, net=None, nvec=8, truncate=True, opts=gl,
+                                                     allow_noconv=True))
+        gcr["no_network"] = {"nvec": 8, "basis": "window", "seconds": t_g0, "iters": stg0["iters"],
+                             "true_residual": stg0["true_residual"], "status": stg0["status"]}
+        extra["gcr"] = gcr
+        if gnet is not net:
+            gnet.close()
     if not args.quick and args.method == "cgne":
         # learned preconditioner: pairs from the solver, Adam, then preconditioned solves
         net = Net(lat, channels=2)
@@ -431,14 +471,15 @@ def main():
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": ("f32 + bf16 tensor-core network (FP64 residual restarts)" if args.method == "learned" else
+        "dtype": ("f32 + bf16 tensor-core network (FP64 residual restarts)" if args.method != "cgne" else
                   {"single": "f32 (FP64 reliable updates)", "half": "f16 storage/f32 (FP64 reliable updates)",
                    "double": "f64"}[args.prec]),
         "data": "synthetic",
         "config": dict(WORKLOAD, prec=args.prec, delta=args.delta, l2="inputs larger than L2 (each solve streams >1 GB)",
                        parallelism=f"replicas x{world}"),
         "solve": {"iters": stats[-1]["iters"], "reliable_updates": stats[-1]["reliable_updates"],
-                  "true_residual": max(s["true_residual"] for s in stats)},
+                  "true_residual": max(s["true_residual"] for s in stats),
+                  "step_seconds_rank0": step_s, "median_step_seconds_rank0": statistics.median(step_s)},
         "fp64_plain": fp64,
         "speedup_vs_fp64": (fp64["seconds"] / value) if fp64 else None,
         "roofline": roof,
@@ -450,6 +491,9 @@ def main():
         "autotune": tune_report,
         "method": {"learned": "CGNE on S M with the trained gauge-equivariant network M (BF16 tensor-core "
                               "channel mixing), FP32 inner cycles restarted from the FP64 residual",
+                   "gcr": f"flexible GCR ({args.nvec} directions, {'sliding window' if args.truncate else 'restarted'}) "
+                          "on S right-preconditioned by the trained network, FP32 inner cycles restarted from the "
+                          "FP64 residual",
                    "cgne": f"CGNE, inner {args.prec}, FP64 reliable updates"}[args.method],
         "learned_setup": learned_setup,
         "cgne_same_run": other,

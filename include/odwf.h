@@ -189,6 +189,20 @@ int odwf_net_train(odwf_net_t* net, int steps, double lr, double* losses, void* 
  * whenever it has dropped by opts->delta. */
 int eofa_solve_learned(odwf_t* h, odwf_net_t* net, double m1, double m2, const void* b, void* x,
                        const odwf_solve_opts* opts, odwf_solve_stats* stats, void* stream);
+/* H_T(m1, m2) x = b like eofa_solve, with flexible GCR on the even-odd Schur system S (Sec. 2, the
+ * even-odd preconditioned D_T), right-preconditioned by the network (net may be NULL: plain GCR).
+ * Not in the paper, which solves with CG. Each step applies the network and S once and
+ * orthonormalises the new direction S z (classical Gram-Schmidt) against a basis of up to nvec - 1
+ * earlier ones (1 <= nvec <= 16): truncate = 0 restarts with an empty basis every nvec steps,
+ * truncate = 1 keeps the last nvec - 1 directions (sliding window). FP32 inner iteration whose
+ * residual is replaced by the FP64 true residual whenever it has dropped by opts->delta;
+ * stats->reliable_updates counts those replacements. Allocates 2 nvec + 3 FP32 half fields on the
+ * handle (kept until odwf_destroy). Returns ODWF_EINVAL for nvec outside 1..16 or masses outside
+ * (0, 1], ODWF_ENOCONV if opts->maxiter steps end above tol, ODWF_ETIMEOUT if opts->max_seconds
+ * (> 0, checked every nvec steps) ran out; x and stats then hold the last iterate and its true
+ * residual. */
+int eofa_solve_gcr(odwf_t* h, odwf_net_t* net, double m1, double m2, const void* b, void* x, int nvec, int truncate,
+                   const odwf_solve_opts* opts, odwf_solve_stats* stats, void* stream);
 
 /* Autotuner: times the launch choices (grid size: one resident wave, one CTA per site group, two or
  * four waves; per-thread neighbour gathers or bulk-staged gathers) of the four fused kernels of the

@@ -31,7 +31,7 @@ EXPORTS = ["odwf_create", "odwf_destroy", "odwf_last_error", "odwf_set_gauge", "
            "odwf_omega_vector", "odwf_profile_enable", "odwf_profile_read", "eofa_mp_terms",
            "odwf_apply_noalloc", "eofa_solve_multi", "odwf_net_create", "odwf_net_destroy",
            "odwf_net_num_params", "odwf_net_weights", "odwf_net_apply", "odwf_net_set_pairs", "odwf_net_loss_grad",
-           "odwf_net_train", "eofa_solve_learned", "odwf_autotune"]
+           "odwf_net_train", "eofa_solve_learned", "odwf_autotune", "eofa_solve_gcr"]
 
 
 class OdwfError(RuntimeError):
@@ -108,6 +108,7 @@ def load_library(path: str = LIB_PATH):
     lib.odwf_net_loss_grad.argtypes = [vp, dp, dp, vp]
     lib.odwf_net_train.argtypes = [vp, i, d, dp, vp]
     lib.eofa_solve_learned.argtypes = [vp, vp, d, d, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), vp]
+    lib.eofa_solve_gcr.argtypes = [vp, vp, d, d, vp, vp, i, i, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), vp]
     lib.eofa_solve_multi.argtypes = [ctypes.POINTER(vp), i, dp, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                      ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), vp]
     _lib = lib
@@ -210,6 +211,24 @@ class ODWF:
         rc = self.lib.eofa_solve(self.h, float(m1), float(m2), _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(st),
                                  _stream_ptr(stream))
         self._check(rc, allow=(ODWF_ENOCONV,) if allow_noconv else ())
+        d = st.as_dict()
+        d["status"] = rc
+        return x, d
+
+    def solve_gcr(self, b, m1, m2, net=None, nvec=8, truncate=False, opts=None, stream=None, allow_noconv=False):
+        """x = H_T(m1, m2)^{-1} b by flexible GCR on S, right-preconditioned by `net` (a Net, or None
+        for plain GCR), with a basis of nvec directions (restarted, or a sliding window when
+        truncate); returns (x, stats dict). With allow_noconv, a solve that ends above tol (maxiter or
+        max_seconds) returns its stats with "status" instead of raising."""
+        import torch
+        self._field(b, self.shape5)
+        x = torch.empty_like(b)
+        st = SolveStats()
+        o = opts if opts is not None else solve_opts(prec="single", delta=1e-3)
+        rc = self.lib.eofa_solve_gcr(self.h, net.n if net is not None else None, float(m1), float(m2), _ptr(b),
+                                     _ptr(x), int(nvec), int(bool(truncate)), ctypes.byref(o), ctypes.byref(st),
+                                     _stream_ptr(stream))
+        self._check(rc, allow=(ODWF_ENOCONV, ODWF_ETIMEOUT) if allow_noconv else ())
         d = st.as_dict()
         d["status"] = rc
         return x, d

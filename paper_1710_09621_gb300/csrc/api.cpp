@@ -357,6 +357,7 @@ int odwf_destroy(odwf_t* h) {
     cudaFree(h->bargs);
     if (h->bstate_host) cudaFreeHost(h->bstate_host);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->gcr_free) h->gcr_free(h->gcr);
     delete h;
     return ODWF_OK;
 }

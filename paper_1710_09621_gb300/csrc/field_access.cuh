@@ -138,4 +138,51 @@ struct Links<ST_FLOAT> {
 template <>
 struct Links<ST_HALF> : Links<ST_FLOAT> {};
 
+// Rows of 24 reals (one (site, s) spinor) in shared memory, moved as 16-byte vectors. Every row
+// start is 16-byte aligned: rows are 96 (FP32) or 192 (FP64) bytes and the staging buffers start at
+// 16-byte aligned offsets.
+__device__ __forceinline__ void row24_store(float* dst, const float* v) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+        reinterpret_cast<float4*>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+__device__ __forceinline__ void row24_store(double* dst, const double* v) {
+#pragma unroll
+    for (int q = 0; q < 12; ++q) reinterpret_cast<double2*>(dst)[q] = make_double2(v[2 * q], v[2 * q + 1]);
+}
+__device__ __forceinline__ void row4_load(const float* p, float* o) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    o[0] = t.x, o[1] = t.y, o[2] = t.z, o[3] = t.w;
+}
+__device__ __forceinline__ void row4_load(const double* p, double* o) {
+    const double2 t0 = reinterpret_cast<const double2*>(p)[0], t1 = reinterpret_cast<const double2*>(p)[1];
+    o[0] = t0.x, o[1] = t0.y, o[2] = t1.x, o[3] = t1.y;
+}
+
+// Fifth-dimension mixing of one site's Ns rows staged in shared memory:
+// out_k = sum_{s'} M_c[s][s'] w_{s'}k, with c = P_+ for k < 12 and P_- for k >= 12; mt holds the two
+// matrices transposed (mt[s' Ns + s] for P_+, then P_-).
+template <typename R>
+__device__ __forceinline__ void s_mix(const R* mt, const R* sh_site, int s, int Ns, R* out, bool accumulate) {
+    R acc[24];
+#pragma unroll
+    for (int k = 0; k < 24; ++k) acc[k] = 0;
+    const int NN = Ns * Ns;
+    for (int sp = 0; sp < Ns; ++sp) {
+        const R cp = mt[sp * Ns + s];
+        const R cm = mt[NN + sp * Ns + s];
+        const R* w = sh_site + sp * 24;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            R t[4];
+            row4_load(w + 4 * q, t);
+            const R c = q < 3 ? cp : cm;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[4 * q + i] = fma(c, t[i], acc[4 * q + i]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 24; ++k) out[k] = accumulate ? out[k] + acc[k] : acc[k];
+}
+
 }  // namespace odwf

@@ -133,26 +133,6 @@ __device__ __forceinline__ void hop_dir(const HopArgs& a, const int* n, int cb, 
     reconstruct<MU, +1>(v, w);
 }
 
-// out_k = sum_{s'} M_c[s][s'] w_{s'}k with c = P_+ for k < 12, P_- for k >= 12 (mt transposed)
-template <typename R>
-__device__ __forceinline__ void s_mix(const R* mt, const R* sh_site, int s, int Ns, R* out, bool accumulate) {
-    R acc[24];
-#pragma unroll
-    for (int k = 0; k < 24; ++k) acc[k] = 0;
-    const int NN = Ns * Ns;
-    for (int sp = 0; sp < Ns; ++sp) {
-        const R cp = mt[sp * Ns + s];
-        const R cm = mt[NN + sp * Ns + s];
-        const R* w = sh_site + sp * 24;
-#pragma unroll
-        for (int k = 0; k < 12; ++k) acc[k] = fma(cp, w[k], acc[k]);
-#pragma unroll
-        for (int k = 12; k < 24; ++k) acc[k] = fma(cm, w[k], acc[k]);
-    }
-#pragma unroll
-    for (int k = 0; k < 24; ++k) out[k] = accumulate ? out[k] + acc[k] : acc[k];
-}
-
 __device__ __forceinline__ double block_reduce_sum(double v, double* wsum) {
     const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
     const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
@@ -343,17 +323,13 @@ __device__ __forceinline__ void hop_body(const HopArgs& a) {
             }
         }
         if (MIXHOP) {
-            R* dst = sh + (ls * Ns + s) * 24;
-#pragma unroll
-            for (int k = 0; k < 24; ++k) dst[k] = v[k];
+            row24_store(sh + (ls * Ns + s) * 24, v);
             __syncthreads();
             s_mix(mh, sh + ls * Ns * 24, s, Ns, v, false);
         }
         if (MIXOWN) {
             if (MIXHOP) __syncthreads();
-            R* dst = sh + (ls * Ns + s) * 24;
-#pragma unroll
-            for (int k = 0; k < 24; ++k) dst[k] = ow[k];
+            row24_store(sh + (ls * Ns + s) * 24, ow);
             __syncthreads();
             s_mix(mo, sh + ls * Ns * 24, s, Ns, v, true);
         }
@@ -630,17 +606,13 @@ __device__ __forceinline__ void hop_body_staged(const HopArgs& a) {
         }
         __syncthreads();  // slots are read; the mixing buffer may overwrite them
         if (MIXHOP) {
-            float* dst = sh + (ls * Ns + s) * 24;
-#pragma unroll
-            for (int k = 0; k < 24; ++k) dst[k] = v[k];
+            row24_store(sh + (ls * Ns + s) * 24, v);
             __syncthreads();
             s_mix(mh, sh + ls * Ns * 24, s, Ns, v, false);
         }
         if (MIXOWN) {
             if (MIXHOP) __syncthreads();
-            float* dst = sh + (ls * Ns + s) * 24;
-#pragma unroll
-            for (int k = 0; k < 24; ++k) dst[k] = ow[k];
+            row24_store(sh + (ls * Ns + s) * 24, ow);
             __syncthreads();
             s_mix(mo, sh + ls * Ns * 24, s, Ns, v, true);
         }

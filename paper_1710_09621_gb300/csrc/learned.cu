@@ -94,12 +94,15 @@ __global__ void __launch_bounds__(256) k_net_layer(NetLayerArgs a) {
     const int gid = lane >> 2, tig = lane & 3;
     constexpr int NCOL = 8 * COUT;
     constexpr int KT = CIN * 4;
-    // shared memory: [mix 2 Ns^2 floats][X rows * kXStride bf16][Y rows * (NCOL+1) floats][sh spb*Ns*24 floats]
+    // shared memory: [mix 2 Ns^2 floats][X rows * kXStride bf16][Y COUT * rows * 9 floats]; the
+    // s-mixing buffer sh (spb Ns 24 floats, 96 bytes per thread) reuses X (144 bytes per thread),
+    // which is dead once every warp has passed the barrier that follows its k loop. Y is channel
+    // major (rows of 8 + 1 pad floats).
     float* mix = reinterpret_cast<float*>(smem_net);
     __nv_bfloat16* X = reinterpret_cast<__nv_bfloat16*>(mix + 2 * Ns * Ns);
     const int rows = nth * 3;
     float* Y = reinterpret_cast<float*>(X + (size_t)rows * kXStride);
-    float* sh = Y + (size_t)rows * (NCOL + 1);
+    float* sh = reinterpret_cast<float*>(X);
     if (a.mix)
         for (int i = tid; i < 2 * Ns * Ns; i += nth) mix[i] = (float)a.mix[i];
     // B fragments for every k-tile and n-tile, kept in registers
@@ -143,12 +146,14 @@ __global__ void __launch_bounds__(256) k_net_layer(NetLayerArgs a) {
                     for (int k = 0; k < 24; ++k) x[k] = 0.f;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    __nv_bfloat16* row = X + (size_t)(tid * 3 + c) * kXStride + j * 8;
-#pragma unroll
-                    for (int sp = 0; sp < 4; ++sp) {
-                        row[sp] = __float2bfloat16_rn(x[(sp * 3 + c) * 2]);
-                        row[4 + sp] = __float2bfloat16_rn(x[(sp * 3 + c) * 2 + 1]);
-                    }
+                    // 8 BF16 (re of spins 0..3, then im) = 16 bytes; the row offset (48 bytes per row,
+                    // 16 per half) and the X base (8 Ns^2 bytes, Ns even) keep it 16-byte aligned
+                    uint4 v;
+                    v.x = pack_bf16(x[(0 * 3 + c) * 2], x[(1 * 3 + c) * 2]);
+                    v.y = pack_bf16(x[(2 * 3 + c) * 2], x[(3 * 3 + c) * 2]);
+                    v.z = pack_bf16(x[(0 * 3 + c) * 2 + 1], x[(1 * 3 + c) * 2 + 1]);
+                    v.w = pack_bf16(x[(2 * 3 + c) * 2 + 1], x[(3 * 3 + c) * 2 + 1]);
+                    *reinterpret_cast<uint4*>(X + (size_t)(tid * 3 + c) * kXStride + j * 8) = v;
                 }
             }
             __syncwarp();
@@ -169,8 +174,8 @@ __global__ void __launch_bounds__(256) k_net_layer(NetLayerArgs a) {
             const int r0 = warp * 96 + m * 16;
 #pragma unroll
             for (int nt = 0; nt < COUT; ++nt) {
-                float* y0 = Y + (size_t)(r0 + gid) * (NCOL + 1) + nt * 8 + 2 * tig;
-                float* y8 = Y + (size_t)(r0 + gid + 8) * (NCOL + 1) + nt * 8 + 2 * tig;
+                float* y0 = Y + (size_t)nt * rows * 9 + (size_t)(r0 + gid) * 9 + 2 * tig;
+                float* y8 = Y + (size_t)nt * rows * 9 + (size_t)(r0 + gid + 8) * 9 + 2 * tig;
                 y0[0] = acc[m][nt][0];
                 y0[1] = acc[m][nt][1];
                 y8[0] = acc[m][nt][2];
@@ -206,7 +211,7 @@ __global__ void __launch_bounds__(256) k_net_layer(NetLayerArgs a) {
             float v[24];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const float* yr = Y + (size_t)(tid * 3 + c) * (NCOL + 1) + co * 8;
+                const float* yr = Y + (size_t)co * rows * 9 + (size_t)(tid * 3 + c) * 9;
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
                     v[(b * 3 + c) * 2] = a.c_hop * yr[b];
@@ -218,29 +223,162 @@ __global__ void __launch_bounds__(256) k_net_layer(NetLayerArgs a) {
                 for (int k = 0; k < 24; ++k) v[k] += wown[k];
             if (a.mix) {
                 __syncthreads();
-                float* dst = sh + (ls * Ns + s) * 24;
-#pragma unroll
-                for (int k = 0; k < 24; ++k) dst[k] = v[k];
+                row24_store(sh + (ls * Ns + s) * 24, v);
                 __syncthreads();
-                float accm[24];
-#pragma unroll
-                for (int k = 0; k < 24; ++k) accm[k] = 0.f;
-                const float* site = sh + ls * Ns * 24;
-                for (int sp = 0; sp < Ns; ++sp) {
-                    const float cp = mix[sp * Ns + s], cm = mix[Ns * Ns + sp * Ns + s];
-#pragma unroll
-                    for (int k = 0; k < 12; ++k) accm[k] = fmaf(cp, site[sp * 24 + k], accm[k]);
-#pragma unroll
-                    for (int k = 12; k < 24; ++k) accm[k] = fmaf(cm, site[sp * 24 + k], accm[k]);
-                }
-#pragma unroll
-                for (int k = 0; k < 24; ++k) v[k] = accm[k];
+                s_mix(mix, sh + ls * Ns * 24, s, Ns, v, false);
             }
             if (!a.own_in_mix && co == 0)
 #pragma unroll
                 for (int k = 0; k < 24; ++k) v[k] += wown[k];
             if (valid) Store<ST_FLOAT>::store(a.out[co], nullptr, (size_t)cb, s, Ns, v);
         }
+    }
+}
+
+// Second layer (2 input channels, 1 output) with the channel mixing BEFORE the transport. Spin
+// weights and colour transport act on different indices, so W[c,d] T_d v_c = T_d (W[c,d] v_c) with
+// both applied at the neighbour: per direction d the gathered v_0(x+d), v_1(x+d) form one K = 16
+// tensor-core step (2 channels x 4 spins x re/im) giving phi_d, which then takes one FP32 transport
+// by U_d. That is 8 transports per (site, s) instead of 16. B is direction-major here: k-tile d
+// holds W[c,d] for c = 0, 1 (rows c * 8 + spin (re), c * 8 + 4 + spin (im)).
+__global__ void __launch_bounds__(256) k_net_layer_mt(NetLayerArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_net[];
+    const int Ns = a.Ns;
+    const int s = threadIdx.x, ls = threadIdx.y, spb = blockDim.y;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int gid = lane >> 2, tig = lane & 3;
+    // shared memory as k_net_layer<2, 1>: [mix][X rows * kXStride bf16][Y rows * 9 floats]; sh reuses X
+    float* mix = reinterpret_cast<float*>(smem_net);
+    __nv_bfloat16* X = reinterpret_cast<__nv_bfloat16*>(mix + 2 * Ns * Ns);
+    const int rows = nth * 3;
+    float* Y = reinterpret_cast<float*>(X + (size_t)rows * kXStride);
+    float* sh = reinterpret_cast<float*>(X);
+    if (a.mix)
+        for (int i = tid; i < 2 * Ns * Ns; i += nth) mix[i] = (float)a.mix[i];
+    uint32_t bfrag[8][2];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        const float* Bt = a.B + (size_t)d * 16 * 8;
+        bfrag[d][0] = pack_bf16(Bt[(2 * tig) * 8 + gid], Bt[(2 * tig + 1) * 8 + gid]);
+        bfrag[d][1] = pack_bf16(Bt[(2 * tig + 8) * 8 + gid], Bt[(2 * tig + 9) * 8 + gid]);
+    }
+    float w0[32];
+    if (a.w0)
+#pragma unroll
+        for (int k = 0; k < 32; ++k) w0[k] = a.w0[k];
+    __syncthreads();
+
+    for (int g = blockIdx.x; g * spb < a.Vh; g += gridDim.x) {
+        __syncthreads();
+        const int cb = g * spb + ls;
+        const bool valid = cb < a.Vh;
+        float v[24];
+#pragma unroll
+        for (int k = 0; k < 24; ++k) v[k] = 0.f;
+#pragma unroll 1
+        for (int d = 0; d < 8; ++d) {
+            const int n = valid ? __ldg(a.nbr + (size_t)cb * 8 + d) : 0;
+            // rows (this thread's 3 colours): [v_0 re s0..3 | v_0 im | v_1 re | v_1 im] as BF16
+#pragma unroll
+            for (int ci = 0; ci < 2; ++ci) {
+                float x[24];
+                if (valid) Store<ST_FLOAT>::load(a.in[ci], nullptr, (size_t)n, s, Ns, x);
+                else
+#pragma unroll
+                    for (int k = 0; k < 24; ++k) x[k] = 0.f;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    uint4 q;
+                    q.x = pack_bf16(x[(0 * 3 + c) * 2], x[(1 * 3 + c) * 2]);
+                    q.y = pack_bf16(x[(2 * 3 + c) * 2], x[(3 * 3 + c) * 2]);
+                    q.z = pack_bf16(x[(0 * 3 + c) * 2 + 1], x[(1 * 3 + c) * 2 + 1]);
+                    q.w = pack_bf16(x[(2 * 3 + c) * 2 + 1], x[(3 * 3 + c) * 2 + 1]);
+                    *reinterpret_cast<uint4*>(X + (size_t)(tid * 3 + c) * kXStride + ci * 8) = q;
+                }
+            }
+            __syncwarp();
+            // phi_d rows = X rows W_d (one k16 step, one n8 tile), to Y (warp-private rows)
+#pragma unroll
+            for (int m = 0; m < 6; ++m) {
+                const int r0 = warp * 96 + m * 16;
+                const uint32_t* x0 = reinterpret_cast<const uint32_t*>(X + (size_t)(r0 + gid) * kXStride);
+                const uint32_t* x8 = reinterpret_cast<const uint32_t*>(X + (size_t)(r0 + gid + 8) * kXStride);
+                uint32_t af[4] = {x0[tig], x8[tig], x0[tig + 4], x8[tig + 4]};
+                float acc[4] = {0.f, 0.f, 0.f, 0.f};
+                mma_bf16(acc, af, bfrag[d]);
+                // scalar stores: rows of 9 floats are only 4-byte aligned
+                float* y0 = Y + (size_t)(r0 + gid) * 9 + 2 * tig;
+                float* y8 = Y + (size_t)(r0 + gid + 8) * 9 + 2 * tig;
+                y0[0] = acc[0];
+                y0[1] = acc[1];
+                y8[0] = acc[2];
+                y8[1] = acc[3];
+            }
+            __syncwarp();
+            // phi_d of this thread (3 colours x 4 spins), then v += U_d phi_d
+            float phi[24], u[18];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float* yr = Y + (size_t)(tid * 3 + c) * 9;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    phi[(b * 3 + c) * 2] = yr[b];
+                    phi[(b * 3 + c) * 2 + 1] = yr[4 + b];
+                }
+            }
+            Links<ST_FLOAT>::load(a.links, cb < a.Vh ? cb : 0, d, u);
+#pragma unroll
+            for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    float re = v[(sp * 3 + i) * 2], im = v[(sp * 3 + i) * 2 + 1];
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        const float ur = u[(i * 3 + j) * 2], ui = u[(i * 3 + j) * 2 + 1];
+                        const float pr = phi[(sp * 3 + j) * 2], pi = phi[(sp * 3 + j) * 2 + 1];
+                        re = fmaf(ur, pr, fmaf(-ui, pi, re));
+                        im = fmaf(ur, pi, fmaf(ui, pr, im));
+                    }
+                    v[(sp * 3 + i) * 2] = re;
+                    v[(sp * 3 + i) * 2 + 1] = im;
+                }
+        }
+        float ow[24];
+        if (a.own && valid) Store<ST_FLOAT>::load(a.own, nullptr, (size_t)cb, s, Ns, ow);
+        else
+#pragma unroll
+            for (int k = 0; k < 24; ++k) ow[k] = 0.f;
+        float wown[24];  // W0 own
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                float re = 0.f, im = 0.f;
+                if (a.w0) {
+#pragma unroll
+                    for (int aa = 0; aa < 4; ++aa) {
+                        const float wr = w0[(b * 4 + aa) * 2], wi = w0[(b * 4 + aa) * 2 + 1];
+                        const float xr = ow[(aa * 3 + c) * 2], xi = ow[(aa * 3 + c) * 2 + 1];
+                        re = fmaf(wr, xr, fmaf(-wi, xi, re));
+                        im = fmaf(wr, xi, fmaf(wi, xr, im));
+                    }
+                }
+                wown[(b * 3 + c) * 2] = re;
+                wown[(b * 3 + c) * 2 + 1] = im;
+            }
+#pragma unroll
+        for (int k = 0; k < 24; ++k) v[k] = a.c_hop * v[k] + (a.own_in_mix ? wown[k] : 0.f);
+        if (a.mix) {
+            __syncthreads();
+            row24_store(sh + (ls * Ns + s) * 24, v);
+            __syncthreads();
+            s_mix(mix, sh + ls * Ns * 24, s, Ns, v, false);
+        }
+        if (!a.own_in_mix)
+#pragma unroll
+            for (int k = 0; k < 24; ++k) v[k] += wown[k];
+        if (valid) Store<ST_FLOAT>::store(a.out[0], nullptr, (size_t)cb, s, Ns, v);
     }
 }
 
@@ -381,7 +519,10 @@ __global__ void k_net_prep(const double* W, int C, float* B0, float* B1, float* 
             cout = which == 2 ? C : 1;
             B = which == 2 ? B2 : B3;
         }
-        const int q = ci * 8 + d, kt = q >> 1, j = q & 1;
+        // C -> 1 layers with C = 2 use the direction-major layout of k_net_layer_mt (k-tile d, half ci);
+        // the others pair two directions of one channel per k-tile
+        const bool dir_major = (cout == 1 && C == 2);
+        const int q = ci * 8 + d, kt = dir_major ? d : q >> 1, j = dir_major ? ci : q & 1;
         const int ncol = 8 * cout;
         float* Bt = B + (size_t)kt * 16 * ncol;
         Bt[(j * 8 + aa) * ncol + co * 8 + b] = (float)wr;
@@ -505,7 +646,7 @@ int grid_for_groups(odwf_s* h, int occ) {
 size_t layer_smem(const odwf_s* h, int cout) {
     const int spb = spb_for(h->Ns), nth = spb * h->Ns, rows = nth * 3;
     return sizeof(float) * 2 * h->Ns * h->Ns + sizeof(__nv_bfloat16) * (size_t)rows * kXStride +
-           sizeof(float) * (size_t)rows * (8 * cout + 1) + sizeof(float) * (size_t)spb * h->Ns * 24;
+           sizeof(float) * (size_t)rows * 9 * cout;
 }
 
 // one layer; `parity` is the output parity
@@ -546,7 +687,7 @@ int net_layer(odwf_net_s* n, int parity, int cin, int cout, const float* const* 
         return cuda_check(h, cudaGetLastError(), "k_net_layer");
     };
     if (cin == 1 && cout == 2) return launch(k_net_layer<1, 2>);
-    if (cin == 2 && cout == 1) return launch(k_net_layer<2, 1>);
+    if (cin == 2 && cout == 1) return launch(k_net_layer_mt);
     if (cin == 1 && cout == 1) return launch(k_net_layer<1, 1>);
     return net_err(n, ODWF_EINVAL, "unsupported layer shape");
 }
@@ -905,6 +1046,89 @@ int write_state(odwf_s* h, cudaStream_t st) {
     return rc ? rc : cuda_check(h, cudaStreamSynchronize(st), "sync");
 }
 
+// b' = R5 g5 b (ABI field b), |b'|^2, b_hat = b'_e + 1/2 H_eo A^{-1} b'_o; x_e = 0, r64 = b_hat and
+// |r64|^2. All FP64, in the handle's workspace.
+int schur_start(odwf_s* h, const SCoef* c, const void* b, double* bnorm2, double* rr64, cudaStream_t st) {
+    Workspace& w = h->ws;
+    const size_t b64 = half_elems_bytes(h, ST_DOUBLE);
+    int rc;
+    if ((rc = launch_pack5(h, (const double*)b, w.b_e, w.b_o, ST_DOUBLE, 1, st))) return rc;
+    if ((rc = launch_norm2(h, w.b_e, ST_DOUBLE, nullptr, 0, st))) return rc;
+    if ((rc = launch_norm2(h, w.b_o, ST_DOUBLE, nullptr, 1, st))) return rc;
+    if ((rc = launch_smix(h, ST_DOUBLE, w.b_o, w.t64, coef_mat(c, 2, h->Ns), 1.0, st))) return rc;
+    {
+        HopArgs a{};
+        a.in = w.t64;
+        a.own = w.b_e;
+        a.out = w.bh;
+        a.a_own = 1.0;
+        a.c_hop = 0.5;
+        if ((rc = launch_hop(h, ST_DOUBLE, 0, false, true, false, EPI_STORE, a, st))) return rc;
+    }
+    if ((rc = read_state(h, st))) return rc;
+    *bnorm2 = h->state_host->result[0] + h->state_host->result[1];
+    if ((rc = cuda_check(h, cudaMemsetAsync(w.x_e, 0, b64, st), "memset"))) return rc;
+    if ((rc = cuda_check(h, cudaMemcpyAsync(w.r64, w.bh, b64, cudaMemcpyDeviceToDevice, st), "copy"))) return rc;
+    if ((rc = launch_norm2(h, w.r64, ST_DOUBLE, nullptr, 3, st))) return rc;
+    if ((rc = read_state(h, st))) return rc;
+    *rr64 = h->state_host->result[3];
+    return ODWF_OK;
+}
+
+// x_o = A^{-1}(b'_o + 1/2 H_oe x_e), the FP64 true residual |b' - D x|/|b'| of both parities, and
+// the unpacked solution x (ABI layout).
+int schur_finish(odwf_s* h, const SCoef* c, void* x, double bnorm2, double* res, cudaStream_t st) {
+    Workspace& w = h->ws;
+    int rc;
+    HopArgs a{};
+    a.in = w.x_e;
+    a.own = w.b_o;
+    a.out = w.x_o;
+    a.a_own = 1.0;
+    a.c_hop = 0.5;
+    a.mhop = coef_mat(c, 2, h->Ns);
+    if ((rc = launch_hop(h, ST_DOUBLE, 1, true, true, false, EPI_STORE, a, st))) return rc;
+    HopArgs r2{};
+    r2.mown = coef_mat(c, 0, h->Ns);
+    r2.c_hop = -0.5;
+    r2.in = w.x_o;
+    r2.own = w.x_e;
+    r2.x = w.b_e;
+    r2.out = w.r64;
+    r2.slot = 0;
+    if ((rc = launch_hop(h, ST_DOUBLE, 0, false, true, true, EPI_RESID, r2, st))) return rc;
+    r2.in = w.x_e;
+    r2.own = w.x_o;
+    r2.x = w.b_o;
+    r2.out = w.t64;
+    r2.slot = 1;
+    if ((rc = launch_hop(h, ST_DOUBLE, 1, false, true, true, EPI_RESID, r2, st))) return rc;
+    if ((rc = launch_unpack5(h, w.x_e, w.x_o, (double*)x, ST_DOUBLE, 0, st))) return rc;
+    if ((rc = read_state(h, st))) return rc;
+    *res = std::sqrt((h->state_host->result[0] + h->state_host->result[1]) / bnorm2);
+    return ODWF_OK;
+}
+
+// S in FP32 on even fields: out = A in - 1/4 H_eo A^{-1} H_oe in (tmp: odd scratch); dag: S^dag
+int schur32(odwf_s* h, const SCoef* c, const float* in, float* tmp, float* out, bool dag, cudaStream_t st) {
+    HopArgs a{};
+    a.in = in;
+    a.out = tmp;
+    a.mhop = coef_mat(c, dag ? 6 : 2, h->Ns);
+    a.c_hop = 1.0;
+    a.g5 = dag ? G5_HOP_IN : 0;
+    int rc = launch_hop(h, ST_FLOAT, 1, true, false, false, EPI_STORE, a, st);
+    if (rc) return rc;
+    HopArgs b2{};
+    b2.in = tmp;
+    b2.own = in;
+    b2.out = out;
+    b2.mown = coef_mat(c, dag ? 4 : 0, h->Ns);
+    b2.c_hop = -0.25;
+    b2.g5 = dag ? (G5_OWN_IN | G5_OUT) : 0;
+    return launch_hop(h, ST_FLOAT, 0, false, true, true, EPI_STORE, b2, st);
+}
+
 }  // namespace
 
 extern "C" int eofa_solve_learned(odwf_t* h, odwf_net_t* n, double m1, double m2, const void* b, void* x,
@@ -925,49 +1149,12 @@ extern "C" int eofa_solve_learned(odwf_t* h, odwf_net_t* n, double m1, double m2
     Workspace& w = h->ws;
     const size_t b64 = half_elems_bytes(h, ST_DOUBLE), b32 = half32(h);
     float *z = n->f[3], *wv = n->f[4], *mv = n->f[5], *xi = n->f[6], *rho = n->f[7], *p = n->sf[0], *t = n->sf[1];
-    // b' = R5 g5 b ; |b'|^2 ; b_hat
-    if ((rc = launch_pack5(h, (const double*)b, w.b_e, w.b_o, ST_DOUBLE, 1, st))) return rc;
-    if ((rc = launch_norm2(h, w.b_e, ST_DOUBLE, nullptr, 0, st))) return rc;
-    if ((rc = launch_norm2(h, w.b_o, ST_DOUBLE, nullptr, 1, st))) return rc;
-    if ((rc = launch_smix(h, ST_DOUBLE, w.b_o, w.t64, coef_mat(c, 2, h->Ns), 1.0, st))) return rc;
-    {
-        HopArgs a{};
-        a.in = w.t64;
-        a.own = w.b_e;
-        a.out = w.bh;
-        a.a_own = 1.0;
-        a.c_hop = 0.5;
-        if ((rc = launch_hop(h, ST_DOUBLE, 0, false, true, false, EPI_STORE, a, st))) return rc;
-    }
-    if ((rc = read_state(h, st))) return rc;
-    const double bnorm2 = h->state_host->result[0] + h->state_host->result[1];
+    double bnorm2 = 0.0, rr64 = 0.0;
+    if ((rc = schur_start(h, c, b, &bnorm2, &rr64, st))) return rc;
     const double tol2 = o.tol * o.tol * bnorm2;
-    if ((rc = cuda_check(h, cudaMemsetAsync(w.x_e, 0, b64, st), "memset"))) return rc;
-    if ((rc = cuda_check(h, cudaMemcpyAsync(w.r64, w.bh, b64, cudaMemcpyDeviceToDevice, st), "copy"))) return rc;
-    if ((rc = launch_norm2(h, w.r64, ST_DOUBLE, nullptr, 3, st))) return rc;
-    if ((rc = read_state(h, st))) return rc;
-    double rr64 = h->state_host->result[3];
     int iters = 0, cycles = 0;
     const double delta = (o.delta > 0 && o.delta < 1) ? o.delta : 1e-3;
-    // S and S^dag in FP32 on even fields
-    auto S32 = [&](const float* in, float* out, bool dag) -> int {
-        HopArgs a{};
-        a.in = in;
-        a.out = t;
-        a.mhop = coef_mat(c, dag ? 6 : 2, h->Ns);
-        a.c_hop = 1.0;
-        a.g5 = dag ? G5_HOP_IN : 0;
-        int r2 = launch_hop(h, ST_FLOAT, 1, true, false, false, EPI_STORE, a, st);
-        if (r2) return r2;
-        HopArgs b2{};
-        b2.in = t;
-        b2.own = in;
-        b2.out = out;
-        b2.mown = coef_mat(c, dag ? 4 : 0, h->Ns);
-        b2.c_hop = -0.25;
-        b2.g5 = dag ? (G5_OWN_IN | G5_OUT) : 0;
-        return launch_hop(h, ST_FLOAT, 0, false, true, true, EPI_STORE, b2, st);
-    };
+    auto S32 = [&](const float* in, float* out, bool dag) -> int { return schur32(h, c, in, t, out, dag, st); };
     while (rr64 > tol2 && iters < o.maxiter) {
         // cycle: solve S M y = r64 to relative delta, x_inner = M y accumulated directly
         if ((rc = launch_convert(h, w.r64, ST_DOUBLE, nullptr, rho, ST_FLOAT, nullptr, st))) return rc;
@@ -1034,35 +1221,8 @@ extern "C" int eofa_solve_learned(odwf_t* h, odwf_net_t* n, double m1, double m2
         rr64 = h->state_host->result[3];
         if (!std::isfinite(rr64)) return set_err(h, ODWF_EBREAKDOWN, "non-finite residual");
     }
-    // x_o = A^{-1}(b'_o + 1/2 H_oe x_e) and the FP64 true residual
-    {
-        HopArgs a{};
-        a.in = w.x_e;
-        a.own = w.b_o;
-        a.out = w.x_o;
-        a.a_own = 1.0;
-        a.c_hop = 0.5;
-        a.mhop = coef_mat(c, 2, h->Ns);
-        if ((rc = launch_hop(h, ST_DOUBLE, 1, true, true, false, EPI_STORE, a, st))) return rc;
-        HopArgs r2{};
-        r2.mown = coef_mat(c, 0, h->Ns);
-        r2.c_hop = -0.5;
-        r2.in = w.x_o;
-        r2.own = w.x_e;
-        r2.x = w.b_e;
-        r2.out = w.r64;
-        r2.slot = 0;
-        if ((rc = launch_hop(h, ST_DOUBLE, 0, false, true, true, EPI_RESID, r2, st))) return rc;
-        r2.in = w.x_e;
-        r2.own = w.x_o;
-        r2.x = w.b_o;
-        r2.out = w.t64;
-        r2.slot = 1;
-        if ((rc = launch_hop(h, ST_DOUBLE, 1, false, true, true, EPI_RESID, r2, st))) return rc;
-    }
-    if ((rc = launch_unpack5(h, w.x_e, w.x_o, (double*)x, ST_DOUBLE, 0, st))) return rc;
-    if ((rc = read_state(h, st))) return rc;
-    const double res = std::sqrt((h->state_host->result[0] + h->state_host->result[1]) / bnorm2);
+    double res = 0.0;
+    if ((rc = schur_finish(h, c, x, bnorm2, &res, st))) return rc;
     if (stats) {
         stats->iters = iters;
         stats->reliable_updates = cycles;
@@ -1070,5 +1230,315 @@ extern "C" int eofa_solve_learned(odwf_t* h, odwf_net_t* n, double m1, double m2
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
     if (!(res <= o.tol)) return set_err(h, ODWF_ENOCONV, "preconditioned solve did not reach tol");
+    return ODWF_OK;
+}
+
+// ---- flexible GCR on S, right-preconditioned by the network ---------------------------------------
+// Inner FP32 iteration (basis of nvec directions, restarted when full or kept as a sliding window of
+// the last nvec - 1), with the residual replaced by the FP64
+// true residual b_hat - S x whenever it has dropped by opts->delta (defect correction). Step j:
+//   z_j = M r (r itself without a network), w_j = S z_j, then classical Gram-Schmidt of w_j against
+//   the orthonormal w_0 .. w_{j-1} (the same combination applied to z_j keeps w_j = S z_j), and
+//   e += alpha z_j, r -= alpha w_j with alpha = <w_j, r>. One pass computes all inner products of
+//   step j (<w_i, w_j>, |w_j|^2, <w_j, r>, <w_i, r>); |w_j - sum beta_i w_i|^2 follows from the
+//   orthonormality of the basis and <w_j - sum beta_i w_i, r> from the <w_i, r>.
+namespace odwf {
+
+constexpr int kGcrMax = 16;
+
+struct GcrPtrs {
+    const float4* p[kGcrMax];
+};
+
+template <int NV>
+__device__ __forceinline__ void gcr_block_sum(const float* acc, double* out) {
+    __shared__ double red[8][NV];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        double v = acc[i];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) red[wp][i] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q][threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+// per-block partial sums, doubles [blk][2 (2 K + 2)]: <V_i, w> (i < K), |w|^2 (imaginary part 0),
+// <w, r>, <V_i, r> (i < K)
+template <int K>
+__global__ void __launch_bounds__(256) k_gcr_dots(GcrPtrs V, const float4* __restrict__ w,
+                                                  const float4* __restrict__ r, size_t n4, double* partials) {
+    constexpr int NV = 2 * (2 * K + 2);
+    float acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.f;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n4; k += (size_t)gridDim.x * blockDim.x) {
+        const float4 a = w[k], b = r[k];
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            const float4 v = V.p[i][k];
+            acc[2 * i] += v.x * a.x + v.y * a.y + v.z * a.z + v.w * a.w;
+            acc[2 * i + 1] += v.x * a.y - v.y * a.x + v.z * a.w - v.w * a.z;
+            acc[2 * K + 4 + 2 * i] += v.x * b.x + v.y * b.y + v.z * b.z + v.w * b.w;
+            acc[2 * K + 5 + 2 * i] += v.x * b.y - v.y * b.x + v.z * b.w - v.w * b.z;
+        }
+        acc[2 * K] += a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w;
+        acc[2 * K + 2] += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+        acc[2 * K + 3] += a.x * b.y - a.y * b.x + a.z * b.w - a.w * b.z;
+    }
+    gcr_block_sum<NV>(acc, partials + (size_t)blockIdx.x * NV);
+}
+
+// out[v] = sum over blocks of partials[b][v]; one warp per value
+__global__ void k_gcr_sum(const double* partials, int nblk, int nval, double* out) {
+    const int v = blockIdx.x;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += 32) s += partials[(size_t)b * nval + v];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (threadIdx.x == 0) out[v] = s;
+}
+
+__device__ __forceinline__ float4 cmul_sub(float4 a, float br, float bi, float4 v) {
+    a.x -= br * v.x - bi * v.y;
+    a.y -= br * v.y + bi * v.x;
+    a.z -= br * v.z - bi * v.w;
+    a.w -= br * v.w + bi * v.z;
+    return a;
+}
+
+// w_j, z_j <- (w_j - sum beta_i W_i) / n, (z_j - sum beta_i Z_i) / n; r -= alpha w_j; e += alpha z_j
+// with alpha = <w_j - sum beta_i W_i, r> / n = (<w_j, r> - sum conj(beta_i) <W_i, r>) / n;
+// per-block |r|^2 to rpart. A direction with no component outside the basis is dropped (zeroed).
+template <int K>
+__global__ void __launch_bounds__(256) k_gcr_update(GcrPtrs W, GcrPtrs Z, const double* __restrict__ sums,
+                                                    float4* w, float4* z, float4* r, float4* e, size_t n4,
+                                                    double* rpart) {
+    const double ww = sums[2 * K];
+    double n2 = ww;
+    float br[K > 0 ? K : 1], bi[K > 0 ? K : 1];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        br[i] = (float)sums[2 * i];
+        bi[i] = (float)sums[2 * i + 1];
+        n2 -= sums[2 * i] * sums[2 * i] + sums[2 * i + 1] * sums[2 * i + 1];
+    }
+    double wr = sums[2 * K + 2], wi = sums[2 * K + 3];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        const double b_r = sums[2 * i], b_i = sums[2 * i + 1];
+        const double c_r = sums[2 * K + 4 + 2 * i], c_i = sums[2 * K + 5 + 2 * i];
+        wr -= b_r * c_r + b_i * c_i;
+        wi -= b_r * c_i - b_i * c_r;
+    }
+    float inv = 0.f, ar = 0.f, ai = 0.f;
+    if (ww > 0.0 && n2 > 1e-10 * ww) {
+        const double id = 1.0 / sqrt(n2);
+        inv = (float)id;
+        ar = (float)(wr * id);
+        ai = (float)(wi * id);
+    }
+    float acc[1] = {0.f};
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n4; k += (size_t)gridDim.x * blockDim.x) {
+        float4 a = w[k], c = z[k];
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            a = cmul_sub(a, br[i], bi[i], W.p[i][k]);
+            c = cmul_sub(c, br[i], bi[i], Z.p[i][k]);
+        }
+        a.x *= inv, a.y *= inv, a.z *= inv, a.w *= inv;
+        c.x *= inv, c.y *= inv, c.z *= inv, c.w *= inv;
+        w[k] = a;
+        z[k] = c;
+        float4 rr = cmul_sub(r[k], ar, ai, a);
+        r[k] = rr;
+        acc[0] += rr.x * rr.x + rr.y * rr.y + rr.z * rr.z + rr.w * rr.w;
+        const float4 ee = e[k];
+        e[k] = make_float4(ee.x + ar * c.x - ai * c.y, ee.y + ar * c.y + ai * c.x, ee.z + ar * c.z - ai * c.w,
+                           ee.w + ar * c.w + ai * c.z);
+    }
+    gcr_block_sum<1>(acc, rpart + blockIdx.x);
+}
+
+}  // namespace odwf
+
+namespace {
+
+struct GcrCache {
+    int cap = 0;
+    float* W[kGcrMax] = {nullptr};
+    float* Z[kGcrMax] = {nullptr};
+    float *r = nullptr, *e = nullptr, *t = nullptr;
+    double *partials = nullptr, *sums = nullptr, *host = nullptr;
+    int nblk = 0;
+};
+
+void gcr_release(void* p) {
+    GcrCache* g = static_cast<GcrCache*>(p);
+    if (!g) return;
+    for (int i = 0; i < kGcrMax; ++i) {
+        cudaFree(g->W[i]);
+        cudaFree(g->Z[i]);
+    }
+    cudaFree(g->r);
+    cudaFree(g->e);
+    cudaFree(g->t);
+    cudaFree(g->partials);
+    cudaFree(g->sums);
+    if (g->host) cudaFreeHost(g->host);
+    delete g;
+}
+
+int gcr_ensure(odwf_s* h, int restart, GcrCache** out) {
+    if (!h->gcr) {
+        GcrCache* g = new GcrCache();
+        g->nblk = h->num_sms * 4;
+        h->gcr = g;
+        h->gcr_free = gcr_release;
+        // dots of a step: [nblk][2 (2 K + 2)], K <= kGcrMax - 1: <= 64 nblk; then |r|^2 partials at 64 nblk
+        const size_t pb = sizeof(double) * (size_t)g->nblk * 65;
+        if (cudaMalloc((void**)&g->r, half32(h)) != cudaSuccess || cudaMalloc((void**)&g->e, half32(h)) != cudaSuccess ||
+            cudaMalloc((void**)&g->t, half32(h)) != cudaSuccess || cudaMalloc((void**)&g->partials, pb) != cudaSuccess ||
+            cudaMalloc((void**)&g->sums, sizeof(double) * 128) != cudaSuccess ||
+            cudaMallocHost((void**)&g->host, sizeof(double) * 8) != cudaSuccess)
+            return set_err(h, ODWF_ENOMEM, "GCR work fields");
+    }
+    GcrCache* g = static_cast<GcrCache*>(h->gcr);
+    if (!g->r || !g->e || !g->t || !g->partials || !g->sums || !g->host)
+        return set_err(h, ODWF_ENOMEM, "GCR work fields");
+    for (; g->cap < restart; ++g->cap)
+        if (cudaMalloc((void**)&g->W[g->cap], half32(h)) != cudaSuccess ||
+            cudaMalloc((void**)&g->Z[g->cap], half32(h)) != cudaSuccess)
+            return set_err(h, ODWF_ENOMEM, "GCR basis");
+    *out = g;
+    return ODWF_OK;
+}
+
+template <int K>
+int gcr_step_k(odwf_s* h, GcrCache* g, const int* win, int slot, size_t n4, cudaStream_t st) {
+    GcrPtrs PW{}, PZ{};
+    for (int i = 0; i < K; ++i) {
+        PW.p[i] = reinterpret_cast<const float4*>(g->W[win[i]]);
+        PZ.p[i] = reinterpret_cast<const float4*>(g->Z[win[i]]);
+    }
+    float4* w = reinterpret_cast<float4*>(g->W[slot]);
+    float4* z = reinterpret_cast<float4*>(g->Z[slot]);
+    cudaEvent_t ev = nullptr;
+    if (h->prof) prof_begin(h, 3000100 + K, st, &ev);
+    k_gcr_dots<K><<<g->nblk, 256, 0, st>>>(PW, w, reinterpret_cast<const float4*>(g->r), n4, g->partials);
+    if (h->prof) prof_end(h, 3000100 + K, st, ev);
+    if (h->prof) prof_begin(h, 3000200, st, &ev);
+    k_gcr_sum<<<2 * (2 * K + 2), 32, 0, st>>>(g->partials, g->nblk, 2 * (2 * K + 2), g->sums);
+    if (h->prof) prof_end(h, 3000200, st, ev);
+    if (h->prof) prof_begin(h, 3000300 + K, st, &ev);
+    k_gcr_update<K><<<g->nblk, 256, 0, st>>>(PW, PZ, g->sums, w, z, reinterpret_cast<float4*>(g->r),
+                                             reinterpret_cast<float4*>(g->e), n4, g->partials + 64 * g->nblk);
+    if (h->prof) prof_end(h, 3000300 + K, st, ev);
+    return cuda_check(h, cudaGetLastError(), "GCR step");
+}
+
+// orthogonalisation of the new direction in basis slot `slot` against the K directions in slots
+// win[0 .. K-1] (0 <= K < kGcrMax), and the update of e and r
+int gcr_step(odwf_s* h, GcrCache* g, const int* win, int K, int slot, size_t n4, cudaStream_t st) {
+    switch (K) {
+#define GCR_CASE(KK) \
+    case KK: return gcr_step_k<KK>(h, g, win, slot, n4, st);
+        GCR_CASE(0) GCR_CASE(1) GCR_CASE(2) GCR_CASE(3) GCR_CASE(4) GCR_CASE(5) GCR_CASE(6) GCR_CASE(7)
+        GCR_CASE(8) GCR_CASE(9) GCR_CASE(10) GCR_CASE(11) GCR_CASE(12) GCR_CASE(13) GCR_CASE(14) GCR_CASE(15)
+#undef GCR_CASE
+    }
+    return set_err(h, ODWF_EINVAL, "GCR step out of range");
+}
+
+}  // namespace
+
+extern "C" int eofa_solve_gcr(odwf_t* h, odwf_net_t* n, double m1, double m2, const void* b, void* x, int nvec,
+                              int truncate, const odwf_solve_opts* opts_in, odwf_solve_stats* stats, void* stream) {
+    if (!h || !b || !x || (n && n->h != h)) return set_err(h, ODWF_EINVAL, "bad argument");
+    if (!(m1 > 0.0 && m1 <= 1.0) || !(m2 > 0.0 && m2 <= 1.0)) return set_err(h, ODWF_EINVAL, "masses must lie in (0, 1]");
+    if (nvec < 1 || nvec > kGcrMax) return set_err(h, ODWF_EINVAL, "nvec must lie in 1..16");
+    const int restart = nvec;
+    if (!h->have_gauge) return set_err(h, ODWF_EINVAL, "odwf_set_gauge has not been called");
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t st = (cudaStream_t)stream;
+    odwf_solve_opts o{1e-10, 100000, ODWF_PREC_SINGLE, 1e-3, 0.0};
+    if (opts_in) o = *opts_in;
+    int rc = ensure_workspace(h, ST_DOUBLE);
+    if (rc) return rc;
+    if (n && (rc = net_set_masses(n, m1, m2))) return rc;
+    const SCoef* c = get_coef(h, m1, m2);
+    if (!c) return ODWF_EINVAL;
+    GcrCache* g = nullptr;
+    if ((rc = gcr_ensure(h, restart, &g))) return rc;
+    Workspace& w = h->ws;
+    const size_t b32 = half32(h), n4 = b32 / sizeof(float4);
+    double bnorm2 = 0.0, rr64 = 0.0;
+    if ((rc = schur_start(h, c, b, &bnorm2, &rr64, st))) return rc;
+    const double tol2 = o.tol * o.tol * bnorm2;
+    const double delta = (o.delta > 0 && o.delta < 1) ? o.delta : 1e-3;
+    int iters = 0, cycles = 0;
+    bool timed_out = false;
+    auto elapsed = [&]() { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); };
+    while (rr64 > tol2 && iters < o.maxiter && !timed_out) {
+        if ((rc = launch_convert(h, w.r64, ST_DOUBLE, nullptr, g->r, ST_FLOAT, nullptr, st))) return rc;
+        if ((rc = cuda_check(h, cudaMemsetAsync(g->e, 0, b32, st), "memset"))) return rc;
+        const double target = std::max(0.25 * tol2, delta * delta * rr64);
+        double rr = rr64;
+        long jt = 0;  // steps of this inner solve
+        while (rr > target && iters < o.maxiter && !timed_out) {
+            for (int j = 0; j < restart && iters < o.maxiter; ++j, ++iters, ++jt) {
+                // restarted: slots 0 .. j-1 then slot j; truncated: the last min(jt, nvec - 1) steps' slots
+                int win[kGcrMax], K, slot;
+                if (truncate) {
+                    slot = (int)(jt % nvec);
+                    K = (int)std::min<long>(jt, nvec - 1);
+                    for (int i = 0; i < K; ++i) win[i] = (int)((jt - K + i) % nvec);
+                } else {
+                    slot = j;
+                    K = j;
+                    for (int i = 0; i < K; ++i) win[i] = i;
+                }
+                if (n) {
+                    if ((rc = net_apply_even(n, g->r, g->Z[slot], 0, st))) return rc;
+                } else if ((rc = cuda_check(h, cudaMemcpyAsync(g->Z[slot], g->r, b32, cudaMemcpyDeviceToDevice, st),
+                                            "copy"))) {
+                    return rc;
+                }
+                if ((rc = schur32(h, c, g->Z[slot], g->t, g->W[slot], false, st))) return rc;
+                if ((rc = gcr_step(h, g, win, K, slot, n4, st))) return rc;
+            }
+            k_gcr_sum<<<1, 32, 0, st>>>(g->partials + 64 * g->nblk, g->nblk, 1, g->sums + 64);
+            if ((rc = cuda_check(h, cudaMemcpyAsync(g->host, g->sums + 64, sizeof(double), cudaMemcpyDeviceToHost, st),
+                                 "D2H")))
+                return rc;
+            if ((rc = cuda_check(h, cudaStreamSynchronize(st), "sync"))) return rc;
+            rr = g->host[0];
+            if (!std::isfinite(rr)) return set_err(h, ODWF_EBREAKDOWN, "non-finite GCR residual");
+            timed_out = o.max_seconds > 0.0 && elapsed() > o.max_seconds;
+        }
+        ++cycles;
+        if ((rc = launch_axpy_to64(h, 1.0, g->e, ST_FLOAT, nullptr, (double*)w.x_e, st))) return rc;
+        if ((rc = residual64(h, c, w.bh, w.x_e, w.t64, w.r64, 3, st))) return rc;
+        if ((rc = read_state(h, st))) return rc;
+        rr64 = h->state_host->result[3];
+        if (!std::isfinite(rr64)) return set_err(h, ODWF_EBREAKDOWN, "non-finite residual");
+    }
+    double res = 0.0;
+    if ((rc = schur_finish(h, c, x, bnorm2, &res, st))) return rc;
+    if (stats) {
+        stats->iters = iters;
+        stats->reliable_updates = cycles;
+        stats->true_residual = res;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (!(res <= o.tol))
+        return set_err(h, timed_out ? ODWF_ETIMEOUT : ODWF_ENOCONV,
+                       timed_out ? "GCR solve stopped at max_seconds" : "GCR solve did not reach tol");
     return ODWF_OK;
 }

@@ -145,6 +145,9 @@ struct odwf_s {
     odwf::HopArgs* bargs = nullptr;
     int bargs_cap = 0;
     cudaStream_t cap_stream = nullptr;   // non-default stream used only to capture CUDA graphs
+    // flexible-GCR basis and work fields, kept between calls; released by gcr_free at destroy
+    void* gcr = nullptr;
+    void (*gcr_free)(void*) = nullptr;
     // kernel timing (odwf_profile_*)
     bool prof = false;
     struct ProfRec { int key; cudaEvent_t a, b; };

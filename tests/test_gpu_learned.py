@@ -120,3 +120,36 @@ def test_train_and_solve(env):
     _, st3 = lat.solve(torch.from_numpy(b).cuda(), M1, M2, opts=binding.solve_opts(tol=1e-10, prec="single"))
     print(f"\nloss {losses[0]:.4e} -> {losses[-1]:.4e}; iterations: trained {st['iters']}, "
           f"Neumann {st2['iters']}, plain CGNE {st3['iters']}")
+
+
+@pytest.mark.parametrize("which,truncate", [("none", False), ("neumann", False), ("trained", False),
+                                            ("neumann", True), ("none", True)])
+def test_gcr_solve(env, which, truncate):
+    """Flexible GCR on S, right-preconditioned by the network (or none), restarted or with a sliding
+    window of directions: FP64 true residual 1e-10."""
+    binding, lat, op, U, om = env
+    net = None
+    if which != "none":
+        net = binding.Net(lat, 2)
+        if which == "trained":
+            rs = [torch.from_numpy(inputs.gaussian_spinor5(DIMS, NS, 60 + i)).cuda() for i in range(3)]
+            net.set_pairs(rs, M1, M2, tol=1e-9)
+            net.train(20, 2e-3)
+    b = inputs.gaussian_spinor5(DIMS, NS, 51)
+    x, st = lat.solve_gcr(torch.from_numpy(b).cuda(), M1, M2, net=net, nvec=8, truncate=truncate,
+                          opts=binding.solve_opts(tol=1e-10, prec="single", delta=1e-3))
+    res = np.linalg.norm(b - op.ht(x.cpu().numpy(), M1, M2)) / np.linalg.norm(b)
+    assert st["true_residual"] <= 1e-10 and res <= 1.05e-10
+    print(f"\nGCR({which}, {'window' if truncate else 'restarted'}): {st['iters']} iterations, "
+          f"{st['reliable_updates']} cycles")
+
+
+def test_gcr_rejects_bad_basis_and_reports_noconv(env):
+    binding, lat, op, U, om = env
+    b = torch.from_numpy(inputs.gaussian_spinor5(DIMS, NS, 52)).cuda()
+    for bad in (0, 17):
+        with pytest.raises(binding.OdwfError):
+            lat.solve_gcr(b, M1, M2, nvec=bad)
+    _, st = lat.solve_gcr(b, M1, M2, nvec=4, opts=binding.solve_opts(tol=1e-10, prec="single", maxiter=3),
+                          allow_noconv=True)
+    assert st["status"] == binding.ODWF_ENOCONV and st["iters"] == 3 and st["true_residual"] > 1e-10
