@@ -210,6 +210,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the hot-path pass, batch and learned sections")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch autotuner")
     ap.add_argument("--train-steps", type=int, default=40)
+    ap.add_argument("--lr", type=float, default=2e-3, help="Adam learning rate of the network training")
+    ap.add_argument("--pairs", type=int, default=4, help="training pairs (r, S^{-1} r) from the plain solver")
     ap.add_argument("--method", default="learned", choices=["learned", "gcr", "cgne"],
                     help="timed solver: learned-preconditioned CGNE (default), flexible GCR right-preconditioned "
                          "by the learned network, or plain mixed-precision CGNE")
@@ -269,14 +271,15 @@ def main():
     if args.method in ("learned", "gcr"):
         from paper_1710_09621_gb300.binding import Net
         net = Net(lat, channels=2)
-        rs = [torch.from_numpy(inputs.gaussian_spinor5(DIMS, NS, inputs.seed_for(4, i))).to(dev) for i in range(4)]
+        rs = [torch.from_numpy(inputs.gaussian_spinor5(DIMS, NS, inputs.seed_for(4, i))).to(dev)
+              for i in range(args.pairs)]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         net.set_pairs(rs, MASS, MASS, tol=1e-8)
         t1 = time.perf_counter()
-        losses = net.train(args.train_steps, 2e-3)
+        losses = net.train(args.train_steps, args.lr)
         t2 = time.perf_counter()
-        learned_setup = {"pairs": len(rs), "pair_seconds": t1 - t0, "train_steps": args.train_steps,
+        learned_setup = {"pairs": len(rs), "pair_seconds": t1 - t0, "train_steps": args.train_steps, "lr": args.lr,
                          "train_seconds": t2 - t1, "loss_first": float(losses[0]), "loss_last": float(losses[-1])}
         del rs
         lopts = solve_opts(tol=TOL, prec="single", delta=1e-3)
@@ -349,17 +352,17 @@ def main():
         barrier()
         fp64 = {"seconds": f0.elapsed_time(f1) / 1e3, "iters": st64["iters"], "true_residual": st64["true_residual"]}
 
+    def timed(fn):
+        barrier()
+        t0 = time.perf_counter()
+        out = fn()
+        barrier()
+        return out, time.perf_counter() - t0
+
     # ---- the rest of the hot path on the same lattice --------------------------------------------
     extra = {}
     if not args.quick:
         from paper_1710_09621_gb300.binding import MP_NEW, Net, mp_terms
-
-        def timed(fn):
-            barrier()
-            t0 = time.perf_counter()
-            out = fn()
-            barrier()
-            return out, time.perf_counter() - t0
 
         # one pass of the new-MP EOFA term list (heat-bath, action, force per term), Eq.(new_MP)
         terms = mp_terms(MP_NEW, MASS, [0.1], 1.0)
@@ -467,6 +470,14 @@ def main():
                 "frac": dom["gbs"] / peak, "peak_source": f"hbm_gbs of {peak_kind}", "traffic": None,
                 "alg_bytes_per_launch": dom["alg_bytes"], "avg_launch_us": dom["avg_us"]}
 
+    # the dslash proper (A3 + A4: hop over all Ns slices fused with the fifth-dimension inverse, K1)
+    dsl = [k for k in kern if "hop+A^-1,store" in k["kernel"] and "fp64" not in k["kernel"]]
+    dslash = None
+    if dsl:
+        k1 = max(dsl, key=lambda k: k["total_ms"])
+        dslash = {"kernel": k1["kernel"], "avg_launch_us": k1["avg_us"], "alg_bytes_per_launch": k1["alg_bytes"],
+                  "achieved_gbs": k1["gbs"], "peak_gbs": peak, "frac": k1["gbs"] / peak,
+                  "peak_source": f"hbm_gbs of {peak_kind}"}
     line = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": False,
@@ -483,6 +494,7 @@ def main():
         "fp64_plain": fp64,
         "speedup_vs_fp64": (fp64["seconds"] / value) if fp64 else None,
         "roofline": roof,
+        "dslash": dslash,
         "kernels": kern,
         "e2e": {"value": e2e_value, "unit": "s", "h2d_bytes_per_step": b_host.numel() * 16,
                 "d2h_bytes_per_step": x_host.numel() * 16},

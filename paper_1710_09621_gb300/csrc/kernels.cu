@@ -646,6 +646,17 @@ __global__ void __launch_bounds__(256) k_hop(HopArgs a) {
     hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(a);
 }
 
+// Register-capped copy for the FP32 hop-then-mix variant (K1, K1^dag): at most 64 registers (4 CTAs
+// of 256 or 8 of 128 threads per SM) costs it 8 bytes of spill and buys resident warps for its
+// latency-bound neighbour gathers; the other variants (which would spill more) keep k_hop.
+template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
+__global__ void __launch_bounds__(256, 4) k_hop_lean(HopArgs a) {
+    hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(a);
+}
+
+template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN>
+constexpr bool kLeanHop = ST == ST_FLOAT && HOP && MIXHOP && !OWN && !MIXOWN;
+
 // Several independent systems in one launch: blockIdx.y selects the system's arguments (its own
 // fields, lattice tables, solver state and reduction buffer); blockIdx.x strides over its sites.
 // Systems that are converged or waiting for a host-side update return at once.
@@ -653,6 +664,24 @@ template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
 __global__ void __launch_bounds__(256) k_hop_multi(const HopArgs* __restrict__ args) {
     __shared__ HopArgs sa;
     hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(stage_args(args, &sa));
+}
+
+template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
+__global__ void __launch_bounds__(256, 4) k_hop_multi_lean(const HopArgs* __restrict__ args) {
+    __shared__ HopArgs sa;
+    hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(stage_args(args, &sa));
+}
+
+// the per-thread-gather kernel of a variant, single system and several systems
+template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
+constexpr auto hop_kernel() {
+    if constexpr (kLeanHop<ST, HOP, MIXHOP, OWN, MIXOWN>) return k_hop_lean<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>;
+    else return k_hop<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>;
+}
+template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
+constexpr auto hop_multi_kernel() {
+    if constexpr (kLeanHop<ST, HOP, MIXHOP, OWN, MIXOWN>) return k_hop_multi_lean<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>;
+    else return k_hop_multi<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>;
 }
 
 // ---- launch ------------------------------------------------------------------------------------
@@ -715,8 +744,8 @@ struct KernelPick {
             if (kind == 2) return (const void*)k_hop_staged<ST, MIXHOP, OWN, MIXOWN, EPI>;
             if (kind == 3) return (const void*)k_hop_staged_multi<ST, MIXHOP, OWN, MIXOWN, EPI>;
         }
-        return kind == 1 ? (const void*)k_hop_multi<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>
-                         : (const void*)k_hop<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>;
+        return kind == 1 ? (const void*)hop_multi_kernel<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>()
+                         : (const void*)hop_kernel<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>();
     }
 };
 
@@ -764,7 +793,7 @@ static int launch_multi_one(odwf_s* h, const HopArgs* dev_args, int n, int max_v
             return cuda_check(h, cudaGetLastError(), "k_hop_staged_multi launch");
         }
     }
-    k_hop_multi<ST, HOP, MIXHOP, OWN, MIXOWN, EPI><<<dim3(gx, n), dim3(h->Ns, spb), smem, st>>>(dev_args);
+    hop_multi_kernel<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>()<<<dim3(gx, n), dim3(h->Ns, spb), smem, st>>>(dev_args);
     return cuda_check(h, cudaGetLastError(), "k_hop_multi launch");
 }
 
@@ -789,9 +818,9 @@ static int launch_one(odwf_s* h, int parity, HopArgs a, cudaStream_t st) {
     if (h->prof) prof_begin(h, key, st, &ev0);
     if constexpr (KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::CAN_STAGE) {
         if (stg) k_hop_staged<ST, MIXHOP, OWN, MIXOWN, EPI><<<grid, dim3(Ns, spb), smem, st>>>(a);
-        else k_hop<ST, HOP, MIXHOP, OWN, MIXOWN, EPI><<<grid, dim3(Ns, spb), smem, st>>>(a);
+        else hop_kernel<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>()<<<grid, dim3(Ns, spb), smem, st>>>(a);
     } else {
-        k_hop<ST, HOP, MIXHOP, OWN, MIXOWN, EPI><<<grid, dim3(Ns, spb), smem, st>>>(a);
+        hop_kernel<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>()<<<grid, dim3(Ns, spb), smem, st>>>(a);
     }
     if (h->prof) prof_end(h, key, st, ev0);
     return cuda_check(h, cudaGetLastError(), "k_hop launch");
