@@ -209,9 +209,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the hot-path pass, batch and learned sections")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch autotuner")
-    ap.add_argument("--train-steps", type=int, default=40)
-    ap.add_argument("--lr", type=float, default=2e-3, help="Adam learning rate of the network training")
-    ap.add_argument("--pairs", type=int, default=4, help="training pairs (r, S^{-1} r) from the plain solver")
+    ap.add_argument("--train-steps", type=int, default=200)
+    ap.add_argument("--lr", type=float, default=5e-3, help="Adam learning rate of the network training")
+    ap.add_argument("--pairs", type=int, default=8, help="training pairs (r, S^{-1} r) from the plain solver")
     ap.add_argument("--method", default="learned", choices=["learned", "gcr", "cgne"],
                     help="timed solver: learned-preconditioned CGNE (default), flexible GCR right-preconditioned "
                          "by the learned network, or plain mixed-precision CGNE")
@@ -302,12 +302,14 @@ def main():
     ev0, ev1 = evs[0], evs[-1]
     stats = []
     with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed")  # lets a profiler select the timed solves (ncu --nvtx)
         ev0.record(stream)
         for i in range(args.steps):
             x, st = do_solve(b, x)
             stats.append(st)
             evs[i + 1].record(stream)
         barrier()
+        torch.cuda.nvtx.range_pop()
     prof = lat.profile_read()
     lat.profile(False)
     step_s = [evs[i].elapsed_time(evs[i + 1]) / 1e3 for i in range(args.steps)]
@@ -442,7 +444,7 @@ def main():
         net = Net(lat, channels=2)
         rs = [torch.from_numpy(inputs.gaussian_spinor5(DIMS, NS, inputs.seed_for(4, i))).to(dev) for i in range(4)]
         _, t_pairs = timed(lambda: net.set_pairs(rs, MASS, MASS, tol=1e-8))
-        losses, t_train = timed(lambda: net.train(args.train_steps, 2e-3))
+        losses, t_train = timed(lambda: net.train(args.train_steps, args.lr))
         lopts = solve_opts(tol=TOL, prec="single", delta=1e-3)
         (xl, stl), t_l = timed(lambda: net.solve(b, MASS, MASS, opts=lopts))
         extra["learned"] = {"pairs": len(rs), "pair_seconds": t_pairs, "train_steps": args.train_steps,

@@ -185,4 +185,97 @@ __device__ __forceinline__ void s_mix(const R* mt, const R* sh_site, int s, int 
     for (int k = 0; k < 24; ++k) out[k] = accumulate ? out[k] + acc[k] : acc[k];
 }
 
+// ---- fifth-dimension mixing on the tensor cores, Ns = 16 -----------------------------------------
+// With Ns = 16 a warp holds exactly two sites (its own 32 (site, s) threads), so the mixing of those
+// two sites is warp-local: per chirality c the product D = A_c B of the 16 x 16 matrix A_c with the
+// 16 x 24 block B (rows s, columns = 12 components of chirality c of the two sites) is three m16n8k8
+// TF32 tiles, two k-steps each. FP32 accuracy is kept by the split X = X_hi + X_lo into TF32 parts:
+// D = A_lo B_hi + A_hi B_lo + A_hi B_hi (the A_lo B_lo term, of relative size 2^-22, is dropped).
+// The A fragments (hi and lo) of both chiralities are built once per CTA (s_mix16_afrag); D is
+// written back in place over the staged rows (chirality c only reads and writes components
+// 12 c .. 12 c + 11) and each thread then reads its own row.
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float* d, const uint32_t* a, const uint32_t* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// uint32 entries of the fragment table: [chirality 2][k-step 2][hi, lo][lane 32][4] (a lane's 16-byte
+// reads of one table are consecutive: conflict-free)
+constexpr int kAfrag16Words = 2 * 2 * 32 * 8;
+
+// Fragment table from the transposed matrix pair mt (A_c[s_out][s_in] = mt[c 256 + s_in 16 + s_out]);
+// every thread of the CTA takes a share; the caller synchronises the CTA afterwards.
+__device__ __forceinline__ void s_mix16_afrag(const double* mt, uint32_t* afr, int tid, int nth) {
+    for (int e = tid; e < kAfrag16Words / 2; e += nth) {
+        const int j = e & 3, lane = (e >> 2) & 31, ks = (e >> 7) & 1, c = e >> 8;
+        const int gid = lane >> 2, tig = lane & 3;
+        const int row = gid + ((j & 1) ? 8 : 0), col = ks * 8 + tig + ((j & 2) ? 4 : 0);
+        const float x = (float)mt[c * 256 + col * 16 + row];
+        const uint32_t hi = tf32_rna(x);
+        uint32_t* w = afr + ((c * 2 + ks) * 2 * 32 + lane) * 4 + j;
+        w[0] = hi;
+        w[32 * 4] = tf32_rna(x - __uint_as_float(hi));
+    }
+}
+
+// Collective over the warp (all 32 lanes), after the warp's rows are staged in sh and a __syncwarp:
+// out = [out +] (mixed row of this thread). sh rows are [site][s][24] with Ns = 16.
+__device__ __forceinline__ void s_mix16_tc(const uint32_t* afr, float* sh, int lane, int warp, int row,
+                                           float* out, bool accumulate) {
+    const int gid = lane >> 2, tig = lane & 3;
+    float* base = sh + (size_t)warp * 2 * 16 * 24;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        float acc[3][4];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[q][e] = 0.f;
+            const int col = 8 * q + gid;
+            const float* bp = base + (col >= 12 ? 16 * 24 + col - 12 : col) + c * 12;
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                const uint4* ap = reinterpret_cast<const uint4*>(afr + ((c * 2 + ks) * 2 * 32 + lane) * 4);
+                const uint4 h4 = ap[0], l4 = ap[32];
+                const uint32_t ah[4] = {h4.x, h4.y, h4.z, h4.w}, al[4] = {l4.x, l4.y, l4.z, l4.w};
+                const float b0 = bp[(ks * 8 + tig) * 24], b1 = bp[(ks * 8 + tig + 4) * 24];
+                uint32_t bh[2], bl[2];
+                bh[0] = tf32_rna(b0);
+                bh[1] = tf32_rna(b1);
+                bl[0] = tf32_rna(b0 - __uint_as_float(bh[0]));
+                bl[1] = tf32_rna(b1 - __uint_as_float(bh[1]));
+                mma_tf32(acc[q], al, bh);
+                mma_tf32(acc[q], ah, bl);
+                mma_tf32(acc[q], ah, bh);
+            }
+        }
+        __syncwarp();  // every lane has read chirality c's components before they are overwritten
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int col = 8 * q + 2 * tig;  // even: (col, col + 1) stay within one site
+            float* d0 = base + (col >= 12 ? 16 * 24 + col - 12 : col) + c * 12 + gid * 24;
+            *reinterpret_cast<float2*>(d0) = make_float2(acc[q][0], acc[q][1]);
+            *reinterpret_cast<float2*>(d0 + 8 * 24) = make_float2(acc[q][2], acc[q][3]);
+        }
+    }
+    __syncwarp();
+    const float* r = sh + (size_t)row * 24;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        float t[4];
+        row4_load(r + 4 * q, t);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) out[4 * q + i] = accumulate ? out[4 * q + i] + t[i] : t[i];
+    }
+}
+
 }  // namespace odwf

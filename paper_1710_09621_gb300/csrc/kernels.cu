@@ -14,6 +14,7 @@
 // with C_mu = B_mu^dag unitary: (1 -/+ gamma_mu) psi = [h; -/+ C h], h = psi_up -/+ B psi_dn, so each
 // direction multiplies one 2-spin half spinor by U.
 #include <cstdio>
+#include <type_traits>
 
 #include "field_access.cuh"
 
@@ -261,6 +262,12 @@ __device__ __forceinline__ void epilogue(const HopArgs& a, int cb, int s, typena
     }
 }
 
+// FP32 K1 (hop then mix, no own field): register-capped FMA variant (true) or the uncapped variant
+// with the tensor-core s-mixing (false)
+constexpr bool kLeanK1 = true;
+template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN>
+constexpr bool kLeanHop = kLeanK1 && ST == ST_FLOAT && HOP && MIXHOP && !OWN && !MIXOWN;
+
 template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
 __device__ __forceinline__ void hop_body(const HopArgs& a) {
     using S = Store<ST>;
@@ -269,9 +276,16 @@ __device__ __forceinline__ void hop_body(const HopArgs& a) {
     const int Ns = a.Ns;
     const int s = threadIdx.x, ls = threadIdx.y, spb = blockDim.y;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
-    R* mh = reinterpret_cast<R*>(smem_raw);
+    // FP32 arithmetic at Ns = 16: warp-local tensor-core s-mixing, with its A-fragment tables first
+    // in shared memory; otherwise FMA s-mixing from the matrices mh / mo
+    constexpr bool kTC = std::is_same<R, float>::value && (MIXHOP || MIXOWN) && !kLeanHop<ST, HOP, MIXHOP, OWN, MIXOWN>;
+    const bool tc = kTC && Ns == 16;
+    uint32_t* afr_h = reinterpret_cast<uint32_t*>(smem_raw);
+    uint32_t* afr_o = afr_h + (tc && MIXHOP ? kAfrag16Words : 0);
+    R* mh = reinterpret_cast<R*>(afr_o + (tc && MIXOWN ? kAfrag16Words : 0));
     R* mo = mh + (MIXHOP ? 2 * Ns * Ns : 0);
     R* sh = mo + (MIXOWN ? 2 * Ns * Ns : 0);
+    const int lane = tid & 31, warp = tid >> 5;
     constexpr bool REDUCE = (EPI != EPI_STORE);
 
     if (a.state != nullptr && EPI != EPI_STORE_NORM && EPI != EPI_RESID) {
@@ -280,6 +294,12 @@ __device__ __forceinline__ void hop_body(const HopArgs& a) {
     for (int i = tid; i < 2 * Ns * Ns; i += nth) {
         if (MIXHOP) mh[i] = (R)a.mhop[i];
         if (MIXOWN) mo[i] = (R)a.mown[i];
+    }
+    if constexpr (kTC) {
+        if (tc) {
+            if (MIXHOP) s_mix16_afrag(a.mhop, afr_h, tid, nth);
+            if (MIXOWN) s_mix16_afrag(a.mown, afr_o, tid, nth);
+        }
     }
     double alpha = 0.0, beta = 0.0;
     if (EPI == EPI_CG_A) alpha = a.state->alpha;
@@ -324,14 +344,37 @@ __device__ __forceinline__ void hop_body(const HopArgs& a) {
         }
         if (MIXHOP) {
             row24_store(sh + (ls * Ns + s) * 24, v);
-            __syncthreads();
-            s_mix(mh, sh + ls * Ns * 24, s, Ns, v, false);
+            if constexpr (kTC) {
+                if (tc) {
+                    __syncwarp();
+                    s_mix16_tc(afr_h, sh, lane, warp, ls * Ns + s, v, false);
+                } else {
+                    __syncthreads();
+                    s_mix(mh, sh + ls * Ns * 24, s, Ns, v, false);
+                }
+            } else {
+                __syncthreads();
+                s_mix(mh, sh + ls * Ns * 24, s, Ns, v, false);
+            }
         }
         if (MIXOWN) {
-            if (MIXHOP) __syncthreads();
+            if (MIXHOP) {
+                if (tc) __syncwarp();
+                else __syncthreads();
+            }
             row24_store(sh + (ls * Ns + s) * 24, ow);
-            __syncthreads();
-            s_mix(mo, sh + ls * Ns * 24, s, Ns, v, true);
+            if constexpr (kTC) {
+                if (tc) {
+                    __syncwarp();
+                    s_mix16_tc(afr_o, sh, lane, warp, ls * Ns + s, v, true);
+                } else {
+                    __syncthreads();
+                    s_mix(mo, sh + ls * Ns * 24, s, Ns, v, true);
+                }
+            } else {
+                __syncthreads();
+                s_mix(mo, sh + ls * Ns * 24, s, Ns, v, true);
+            }
         }
         if (g5out) g5_flip(v);
         if (!valid) continue;
@@ -654,8 +697,7 @@ __global__ void __launch_bounds__(256, 4) k_hop_lean(HopArgs a) {
     hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(a);
 }
 
-template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN>
-constexpr bool kLeanHop = ST == ST_FLOAT && HOP && MIXHOP && !OWN && !MIXOWN;
+
 
 // Several independent systems in one launch: blockIdx.y selects the system's arguments (its own
 // fields, lattice tables, solver state and reduction buffer); blockIdx.x strides over its sites.
@@ -754,6 +796,9 @@ static int occupancy(odwf_s* h, int kind, size_t* smem_out) {
     using R = typename Store<ST>::R;
     const int Ns = h->Ns, spb = spb_for(Ns);
     size_t smem = sizeof(R) * ((size_t)(MIXHOP + MIXOWN) * 2 * Ns * Ns + (size_t)spb * Ns * 24);
+    // A-fragment tables of the tensor-core s-mixing (FP32 arithmetic, Ns = 16)
+    if (std::is_same<R, float>::value && Ns == 16 && !kLeanHop<ST, HOP, MIXHOP, OWN, MIXOWN>)
+        smem += sizeof(uint32_t) * kAfrag16Words * (MIXHOP + MIXOWN);
     if constexpr (ST != ST_DOUBLE) {
         if (kind >= 2) smem = staged_smem<ST>(Ns, spb, MIXHOP, MIXOWN);
     }

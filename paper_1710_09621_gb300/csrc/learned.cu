@@ -103,8 +103,13 @@ __global__ void __launch_bounds__(256) k_net_layer(NetLayerArgs a) {
     const int rows = nth * 3;
     float* Y = reinterpret_cast<float*>(X + (size_t)rows * kXStride);
     float* sh = reinterpret_cast<float*>(X);
-    if (a.mix)
+    // Ns = 16: warp-local tensor-core s-mixing with its A-fragment table after Y
+    const bool tc = Ns == 16;
+    uint32_t* afr = reinterpret_cast<uint32_t*>(Y + (size_t)rows * 9 * COUT);
+    if (a.mix) {
         for (int i = tid; i < 2 * Ns * Ns; i += nth) mix[i] = (float)a.mix[i];
+        if (tc) s_mix16_afrag(a.mix, afr, tid, nth);
+    }
     // B fragments for every k-tile and n-tile, kept in registers
     uint32_t bfrag[KT][COUT][2];
 #pragma unroll
@@ -224,8 +229,13 @@ __global__ void __launch_bounds__(256) k_net_layer(NetLayerArgs a) {
             if (a.mix) {
                 __syncthreads();
                 row24_store(sh + (ls * Ns + s) * 24, v);
-                __syncthreads();
-                s_mix(mix, sh + ls * Ns * 24, s, Ns, v, false);
+                if (tc) {
+                    __syncwarp();
+                    s_mix16_tc(afr, sh, lane, warp, ls * Ns + s, v, false);
+                } else {
+                    __syncthreads();
+                    s_mix(mix, sh + ls * Ns * 24, s, Ns, v, false);
+                }
             }
             if (!a.own_in_mix && co == 0)
 #pragma unroll
@@ -254,8 +264,13 @@ __global__ void __launch_bounds__(256) k_net_layer_mt(NetLayerArgs a) {
     const int rows = nth * 3;
     float* Y = reinterpret_cast<float*>(X + (size_t)rows * kXStride);
     float* sh = reinterpret_cast<float*>(X);
-    if (a.mix)
+    // Ns = 16: warp-local tensor-core s-mixing with its A-fragment table after Y
+    const bool tc = Ns == 16;
+    uint32_t* afr = reinterpret_cast<uint32_t*>(Y + (size_t)rows * 9 * 1);
+    if (a.mix) {
         for (int i = tid; i < 2 * Ns * Ns; i += nth) mix[i] = (float)a.mix[i];
+        if (tc) s_mix16_afrag(a.mix, afr, tid, nth);
+    }
     uint32_t bfrag[8][2];
 #pragma unroll
     for (int d = 0; d < 8; ++d) {
@@ -372,8 +387,13 @@ __global__ void __launch_bounds__(256) k_net_layer_mt(NetLayerArgs a) {
         if (a.mix) {
             __syncthreads();
             row24_store(sh + (ls * Ns + s) * 24, v);
-            __syncthreads();
-            s_mix(mix, sh + ls * Ns * 24, s, Ns, v, false);
+            if (tc) {
+                __syncwarp();
+                s_mix16_tc(afr, sh, lane, warp, ls * Ns + s, v, false);
+            } else {
+                __syncthreads();
+                s_mix(mix, sh + ls * Ns * 24, s, Ns, v, false);
+            }
         }
         if (!a.own_in_mix)
 #pragma unroll
@@ -646,7 +666,7 @@ int grid_for_groups(odwf_s* h, int occ) {
 size_t layer_smem(const odwf_s* h, int cout) {
     const int spb = spb_for(h->Ns), nth = spb * h->Ns, rows = nth * 3;
     return sizeof(float) * 2 * h->Ns * h->Ns + sizeof(__nv_bfloat16) * (size_t)rows * kXStride +
-           sizeof(float) * (size_t)rows * 9 * cout;
+           sizeof(float) * (size_t)rows * 9 * cout + (h->Ns == 16 ? sizeof(uint32_t) * kAfrag16Words : 0);
 }
 
 // one layer; `parity` is the output parity

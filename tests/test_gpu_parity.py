@@ -231,4 +231,6 @@ def test_staged_and_plain_kernels_agree(lib, case, monkeypatch):
         lat, op, U, om = _setup(lib, *case)
         outs[staged] = lat.apply(torch.from_numpy(psi).cuda(), 0.05, 0.5, op="dt", prec="single").cpu().numpy()
         lat.close()
-    assert _rel(outs["1"], outs["0"]) < 1e-7
+    # the staged kernels mix the fifth dimension with FP32 FMA, the plain ones at Ns = 16 on the tensor
+    # cores (3xTF32, FP32-accurate): the sums agree to FP32 rounding (an indexing error would be O(1))
+    assert _rel(outs["1"], outs["0"]) < 1e-6
