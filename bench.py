@@ -103,6 +103,17 @@ class ClockSampler:
 # algorithmic bytes per launch of the fused hopping kernels (per 5D half-site: spinor reads and
 # writes of 24 reals, links 8 x 18 reals per 4D half-site shared by Ns slices)
 def alg_bytes(key, Vh, Ns):
+    if key >= 4000000:  # layout / vector kernels: kind, first and second storage (0 FP64, 1 FP32, 2 FP16)
+        kind, s1, s2 = (key // 100) % 10, (key // 10) % 10, key % 10
+        n5 = Vh * Ns
+        fb = {0: 192, 1: 96, 2: 52}  # bytes per 5D half-site (FP16 with its per-site scale)
+        if kind in (1, 2):           # both parities, ABI FP64 <-> internal
+            return 2 * n5 * (fb[s1] + fb[s2])
+        if kind == 3:
+            return n5 * (fb[s1] + fb[s2])
+        if kind == 4:                # read x, read and write y (FP64)
+            return n5 * (fb[s1] + 2 * 192)
+        return n5 * fb[s1]
     if key >= 3000000:  # GCR step kernels (FP32 half fields of Vh Ns 96 bytes)
         kind, k = (key // 100) % 10, key % 100
         fld = Vh * Ns * 96
@@ -135,6 +146,11 @@ def alg_bytes(key, Vh, Ns):
 
 
 def kernel_name(key):
+    if key >= 4000000:
+        kind, s1, s2 = (key // 100) % 10, (key // 10) % 10, key % 10
+        nm = ["fp64", "fp32", "fp16"]
+        return {1: f"k_pack5<{nm[s2]}>", 2: f"k_unpack5<{nm[s1]}>", 3: f"k_convert<{nm[s1]}->{nm[s2]}>",
+                4: f"k_axpy_to64<{nm[s1]}>", 5: f"k_norm2<{nm[s1]}>"}[kind]
     if key >= 3000000:
         kind, k = (key // 100) % 10, key % 100
         return {1: f"k_gcr_dots<{k}>", 2: "k_gcr_sum", 3: f"k_gcr_update<{k}>"}[kind]

@@ -827,11 +827,13 @@ static int launch_multi_one(odwf_s* h, const HopArgs* dev_args, int n, int max_v
     const int occ = occupancy<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(h, kind, &smem);
     const int spb = spb_for(h->Ns);
     const int groups = (max_vh + spb - 1) / spb;
-    int gx = (h->num_sms * occ + n - 1) / n;
-    if (gx < h->num_sms) gx = h->num_sms;
+    // one full resident wave per system: while several systems run their CTAs queue behind one
+    // another, and once the others have stopped (their CTAs return at once) the last running
+    // system still has the whole GPU rather than a 1/n share of it
+    int gx = h->num_sms * occ;
     if (gx > groups) gx = groups;
+    if (EPI != EPI_STORE && gx > h->partials_n) gx = h->partials_n;
     if (gx < 1) gx = 1;
-    if (EPI != EPI_STORE && gx > h->partials_n) return set_err(h, ODWF_EINVAL, "partials buffer too small");
     if constexpr (KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::CAN_STAGE) {
         if (stg) {
             k_hop_staged_multi<ST, MIXHOP, OWN, MIXOWN, EPI><<<dim3(gx, n), dim3(h->Ns, spb), smem, st>>>(dev_args);
@@ -1003,7 +1005,23 @@ static int grid_1d(odwf_s* h, size_t n) {
     return (int)(g < 1 ? 1 : g);
 }
 
+// Kernel timing of the layout and vector launches (odwf_profile_*): key 4000000 + kind * 100 +
+// first storage * 10 + second storage; kind 1 pack5, 2 unpack5, 3 convert, 4 axpy to FP64, 5 norm.
+struct ProfScope {
+    odwf_s* h;
+    int key;
+    cudaStream_t st;
+    cudaEvent_t ev = nullptr;
+    ProfScope(odwf_s* h_, int kind, int s1, int s2, cudaStream_t st_) : h(h_), key(4000000 + kind * 100 + s1 * 10 + s2), st(st_) {
+        if (h->prof) prof_begin(h, key, st, &ev);
+    }
+    ~ProfScope() {
+        if (h->prof) prof_end(h, key, st, ev);
+    }
+};
+
 int launch_pack5(odwf_s* h, const double* lex5, void* e, void* o, int storage, int r5g5, cudaStream_t st) {
+    ProfScope ps(h, 1, ST_DOUBLE, storage, st);
     const size_t n = (size_t)2 * h->Vh * h->Ns;
     const int g = grid_1d(h, n);
     if (storage == ST_DOUBLE)
@@ -1018,6 +1036,7 @@ int launch_pack5(odwf_s* h, const double* lex5, void* e, void* o, int storage, i
 }
 
 int launch_unpack5(odwf_s* h, const void* e, const void* o, double* lex5, int storage, int r5g5, cudaStream_t st) {
+    ProfScope ps(h, 2, storage, ST_DOUBLE, st);
     const size_t n = (size_t)2 * h->Vh * h->Ns;
     const int g = grid_1d(h, n);
     if (storage == ST_DOUBLE)
@@ -1108,10 +1127,12 @@ static int convert_dispatch(odwf_s* h, const void* in, int sti, const float* isc
 
 int launch_convert(odwf_s* h, const void* in, int st_in, const float* in_scale, void* out, int st_out,
                    float* out_scale, cudaStream_t st) {
+    ProfScope ps(h, 3, st_in, st_out, st);
     return convert_dispatch(h, in, st_in, in_scale, out, st_out, out_scale, st);
 }
 
 int launch_axpy_to64(odwf_s* h, double a, const void* x, int st_in, const float* xsc, double* y, cudaStream_t st) {
+    ProfScope ps(h, 4, st_in, ST_DOUBLE, st);
     const int g = grid_1d(h, (size_t)h->Vh * h->Ns);
     if (st_in == ST_FLOAT) k_axpy_to64<ST_FLOAT><<<g, 256, 0, st>>>(a, x, xsc, y, h->Vh, h->Ns);
     else if (st_in == ST_HALF) k_axpy_to64<ST_HALF><<<g, 256, 0, st>>>(a, x, xsc, y, h->Vh, h->Ns);
@@ -1121,6 +1142,7 @@ int launch_axpy_to64(odwf_s* h, double a, const void* x, int st_in, const float*
 
 int launch_norm2(odwf_s* h, const void* v, int storage, const float* sc, int slot, cudaStream_t st,
                  CGState* state, double* partials) {
+    ProfScope ps(h, 5, storage, storage, st);
     int g = grid_1d(h, (size_t)h->Vh * h->Ns);
     if (g > h->partials_n) g = h->partials_n;
     if (!state) state = h->state;
