@@ -32,6 +32,12 @@ WORKLOAD = {"workload": "16^3x32 Ns=16 optimal DWF (Zolotarev omega on [0.05,6.2
                         "links eps=0.3, H_T(m,m) x = b to true residual 1e-10",
             "dims": [16, 16, 16, 32], "Ns": 16, "m0": 1.3, "mass": 0.01, "tol": 1e-10}
 DIMS, NS, M0, MASS, EPS, TOL = (16, 16, 16, 32), 16, 1.3, 0.01, 0.3, 1e-10
+# flop conventions per 5D half-site: the spin-projected Wilson hop (8 directions x [12 projection +
+# 2 x 66 SU(3) matrix-vector + 24 accumulation] - 24), the structured fifth-dimension solve, and one
+# CGNE iteration (4 hops + 4 fifth-dimension solves + 5 BLAS-1 updates x, r, |r|^2, p, |p|^2 of 24
+# reals at 2 flops each)
+HOP_FLOPS, FIFTH_FLOPS = 1320, 240
+CG_ITER_FLOPS = 4 * HOP_FLOPS + 4 * FIFTH_FLOPS + 5 * 2 * 24
 
 
 def reduce_max(value, dist=None, device="cpu"):
@@ -46,6 +52,17 @@ def reduce_max(value, dist=None, device="cpu"):
 def per_solve_seconds(max_elapsed, steps, world):
     """Whole-job seconds per solve: every rank solves `steps` systems in `max_elapsed` seconds."""
     return max_elapsed / (steps * world)
+
+
+def dram_traffic(kernel, dims, ns):
+    """ncu-measured DRAM bytes per launch of `kernel` on this lattice, or None if not captured."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(p):
+        return None
+    for e in json.load(open(p))["entries"]:
+        if e["kernel"] == kernel and tuple(e["dims"]) == tuple(dims) and e["Ns"] == ns:
+            return e["dram_read_bytes"] + e["dram_write_bytes"]
+    return None
 
 
 def peaks():
@@ -485,7 +502,8 @@ def main():
     roof = None
     if dom:
         roof = {"bound": "hbm", "kernel": dom["kernel"], "achieved": dom["gbs"], "peak": peak, "unit": "GB/s",
-                "frac": dom["gbs"] / peak, "peak_source": f"hbm_gbs of {peak_kind}", "traffic": None,
+                "frac": dom["gbs"] / peak, "peak_source": f"hbm_gbs of {peak_kind}",
+                "traffic": dram_traffic(dom["kernel"], DIMS, NS),
                 "alg_bytes_per_launch": dom["alg_bytes"], "avg_launch_us": dom["avg_us"]}
 
     # the dslash proper (A3 + A4: hop over all Ns slices fused with the fifth-dimension inverse, K1)
@@ -495,7 +513,10 @@ def main():
         k1 = max(dsl, key=lambda k: k["total_ms"])
         dslash = {"kernel": k1["kernel"], "avg_launch_us": k1["avg_us"], "alg_bytes_per_launch": k1["alg_bytes"],
                   "achieved_gbs": k1["gbs"], "peak_gbs": peak, "frac": k1["gbs"] / peak,
-                  "peak_source": f"hbm_gbs of {peak_kind}"}
+                  "traffic": dram_traffic(k1["kernel"], DIMS, NS),
+                  "peak_source": f"hbm_gbs of {peak_kind}",
+                  "gflops": Vh * NS * (HOP_FLOPS + FIFTH_FLOPS) / (k1["avg_us"] * 1e-6) / 1e9,
+                  "gflops_convention": f"{HOP_FLOPS} hop + {FIFTH_FLOPS} fifth-dimension flops per 5D half-site"}
     line = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": False,
@@ -528,6 +549,14 @@ def main():
         "learned_setup": learned_setup,
         "cgne_same_run": other,
     }
+    # Krylov throughput in the flop convention of one CGNE iteration (CG_ITER_FLOPS per 5D half-site
+    # of the even checkerboard)
+    for rec in (line["cgne_same_run"], line["fp64_plain"]):
+        if rec and rec.get("seconds"):
+            rec["gflops"] = rec["iters"] * Vh * NS * CG_ITER_FLOPS / rec["seconds"] / 1e9
+            rec["gflops_convention"] = f"{CG_ITER_FLOPS} flops per 5D half-site per CGNE iteration"
+    if args.method == "cgne":
+        line["solve"]["gflops"] = stats[-1]["iters"] * Vh * NS * CG_ITER_FLOPS / value / 1e9
     line.update(extra)
     if rank == 0 and not args.no_cpu and world == 1:
         n_it = fp64["iters"] if fp64 else args.ref_iters

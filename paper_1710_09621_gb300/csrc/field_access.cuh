@@ -159,11 +159,18 @@ __device__ __forceinline__ void row4_load(const double* p, double* o) {
     o[0] = t0.x, o[1] = t0.y, o[2] = t1.x, o[3] = t1.y;
 }
 
-// Fifth-dimension mixing of one site's Ns rows staged in shared memory:
+// Row stride (in reals) of the padded staging rows of the FMA fifth-dimension mixing: 28 floats
+// (112 bytes) or 26 doubles (208 bytes) put the 16-byte row stores of 8 consecutive lanes on 8
+// distinct 4-bank groups, where the unpadded 96 / 192-byte rows collide two- and four-way.
+template <typename R>
+constexpr int kRowStride = sizeof(R) == 4 ? 28 : 26;
+
+// Fifth-dimension mixing of one site's Ns rows staged in shared memory (row stride rs reals):
 // out_k = sum_{s'} M_c[s][s'] w_{s'}k, with c = P_+ for k < 12 and P_- for k >= 12; mt holds the two
 // matrices transposed (mt[s' Ns + s] for P_+, then P_-).
 template <typename R>
-__device__ __forceinline__ void s_mix(const R* mt, const R* sh_site, int s, int Ns, R* out, bool accumulate) {
+__device__ __forceinline__ void s_mix(const R* mt, const R* sh_site, int s, int Ns, R* out, bool accumulate,
+                                      int rs = 24) {
     R acc[24];
 #pragma unroll
     for (int k = 0; k < 24; ++k) acc[k] = 0;
@@ -171,7 +178,7 @@ __device__ __forceinline__ void s_mix(const R* mt, const R* sh_site, int s, int 
     for (int sp = 0; sp < Ns; ++sp) {
         const R cp = mt[sp * Ns + s];
         const R cm = mt[NN + sp * Ns + s];
-        const R* w = sh_site + sp * 24;
+        const R* w = sh_site + sp * rs;
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
             R t[4];

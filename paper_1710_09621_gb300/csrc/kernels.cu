@@ -262,13 +262,22 @@ __device__ __forceinline__ void epilogue(const HopArgs& a, int cb, int s, typena
     }
 }
 
+// Barrier over the threads that share staged rows: the whole CTA, or just the warp when every site
+// lies inside one warp (WS: Ns divides 32, so a site's Ns threads are consecutive lanes of one warp
+// and only they write and read its rows).
+template <bool WS>
+__device__ __forceinline__ void site_barrier() {
+    if constexpr (WS) __syncwarp();
+    else __syncthreads();
+}
+
 // FP32 K1 (hop then mix, no own field): register-capped FMA variant (true) or the uncapped variant
 // with the tensor-core s-mixing (false)
 constexpr bool kLeanK1 = true;
 template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN>
 constexpr bool kLeanHop = kLeanK1 && ST == ST_FLOAT && HOP && MIXHOP && !OWN && !MIXOWN;
 
-template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
+template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI, bool WS>
 __device__ __forceinline__ void hop_body(const HopArgs& a) {
     using S = Store<ST>;
     using R = typename S::R;
@@ -280,6 +289,9 @@ __device__ __forceinline__ void hop_body(const HopArgs& a) {
     // in shared memory; otherwise FMA s-mixing from the matrices mh / mo
     constexpr bool kTC = std::is_same<R, float>::value && (MIXHOP || MIXOWN) && !kLeanHop<ST, HOP, MIXHOP, OWN, MIXOWN>;
     const bool tc = kTC && Ns == 16;
+    // staging row stride: 24 reals for the tensor-core mixing (its fragment loads are laid out for
+    // it), the padded stride for the FMA mixing
+    const int rst = tc ? 24 : kRowStride<R>;
     uint32_t* afr_h = reinterpret_cast<uint32_t*>(smem_raw);
     uint32_t* afr_o = afr_h + (tc && MIXHOP ? kAfrag16Words : 0);
     R* mh = reinterpret_cast<R*>(afr_o + (tc && MIXOWN ? kAfrag16Words : 0));
@@ -307,9 +319,10 @@ __device__ __forceinline__ void hop_body(const HopArgs& a) {
     const bool g5h = (a.g5 & G5_HOP_IN) != 0, g5o = (a.g5 & G5_OWN_IN) != 0, g5out = (a.g5 & G5_OUT) != 0;
     const R chop = (R)a.c_hop, aown = (R)a.a_own;
     double part = 0.0;
+    __syncthreads();  // the matrices (and fragment tables) staged above are visible to every warp
 
     for (int g = blockIdx.x; g * spb < a.Vh; g += gridDim.x) {
-        __syncthreads();
+        site_barrier<WS>();
         const int cb = g * spb + ls;
         const bool valid = cb < a.Vh;
         R v[24];
@@ -343,37 +356,37 @@ __device__ __forceinline__ void hop_body(const HopArgs& a) {
             }
         }
         if (MIXHOP) {
-            row24_store(sh + (ls * Ns + s) * 24, v);
+            row24_store(sh + (ls * Ns + s) * rst, v);
             if constexpr (kTC) {
                 if (tc) {
                     __syncwarp();
                     s_mix16_tc(afr_h, sh, lane, warp, ls * Ns + s, v, false);
                 } else {
-                    __syncthreads();
-                    s_mix(mh, sh + ls * Ns * 24, s, Ns, v, false);
+                    site_barrier<WS>();
+                    s_mix(mh, sh + ls * Ns * rst, s, Ns, v, false, rst);
                 }
             } else {
-                __syncthreads();
-                s_mix(mh, sh + ls * Ns * 24, s, Ns, v, false);
+                site_barrier<WS>();
+                s_mix(mh, sh + ls * Ns * rst, s, Ns, v, false, rst);
             }
         }
         if (MIXOWN) {
             if (MIXHOP) {
                 if (tc) __syncwarp();
-                else __syncthreads();
+                else site_barrier<WS>();
             }
-            row24_store(sh + (ls * Ns + s) * 24, ow);
+            row24_store(sh + (ls * Ns + s) * rst, ow);
             if constexpr (kTC) {
                 if (tc) {
                     __syncwarp();
                     s_mix16_tc(afr_o, sh, lane, warp, ls * Ns + s, v, true);
                 } else {
-                    __syncthreads();
-                    s_mix(mo, sh + ls * Ns * 24, s, Ns, v, true);
+                    site_barrier<WS>();
+                    s_mix(mo, sh + ls * Ns * rst, s, Ns, v, true, rst);
                 }
             } else {
-                __syncthreads();
-                s_mix(mo, sh + ls * Ns * 24, s, Ns, v, true);
+                site_barrier<WS>();
+                s_mix(mo, sh + ls * Ns * rst, s, Ns, v, true, rst);
             }
         }
         if (g5out) g5_flip(v);
@@ -684,17 +697,17 @@ size_t staged_smem(int Ns, int spb, bool mixhop, bool mixown) {
            (size_t)G::nslots(spb) * (G::slot_bytes(Ns) + G::scale_bytes(Ns));
 }
 
-template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
+template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI, bool WS>
 __global__ void __launch_bounds__(256) k_hop(HopArgs a) {
-    hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(a);
+    hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS>(a);
 }
 
 // Register-capped copy for the FP32 hop-then-mix variant (K1, K1^dag): at most 64 registers (4 CTAs
 // of 256 or 8 of 128 threads per SM) costs it 8 bytes of spill and buys resident warps for its
 // latency-bound neighbour gathers; the other variants (which would spill more) keep k_hop.
-template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
+template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI, bool WS>
 __global__ void __launch_bounds__(256, 4) k_hop_lean(HopArgs a) {
-    hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(a);
+    hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS>(a);
 }
 
 
@@ -702,29 +715,32 @@ __global__ void __launch_bounds__(256, 4) k_hop_lean(HopArgs a) {
 // Several independent systems in one launch: blockIdx.y selects the system's arguments (its own
 // fields, lattice tables, solver state and reduction buffer); blockIdx.x strides over its sites.
 // Systems that are converged or waiting for a host-side update return at once.
-template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
+template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI, bool WS>
 __global__ void __launch_bounds__(256) k_hop_multi(const HopArgs* __restrict__ args) {
     __shared__ HopArgs sa;
-    hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(stage_args(args, &sa));
+    hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS>(stage_args(args, &sa));
 }
 
-template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
+template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI, bool WS>
 __global__ void __launch_bounds__(256, 4) k_hop_multi_lean(const HopArgs* __restrict__ args) {
     __shared__ HopArgs sa;
-    hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(stage_args(args, &sa));
+    hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS>(stage_args(args, &sa));
 }
 
-// the per-thread-gather kernel of a variant, single system and several systems
-template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
+// the per-thread-gather kernel of a variant, single system and several systems; WS (Ns divides
+// 32) selects warp-level instead of CTA-wide synchronisation of the staged rows
+template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI, bool WS>
 constexpr auto hop_kernel() {
-    if constexpr (kLeanHop<ST, HOP, MIXHOP, OWN, MIXOWN>) return k_hop_lean<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>;
-    else return k_hop<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>;
+    if constexpr (kLeanHop<ST, HOP, MIXHOP, OWN, MIXOWN>) return k_hop_lean<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS>;
+    else return k_hop<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS>;
 }
-template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
+template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI, bool WS>
 constexpr auto hop_multi_kernel() {
-    if constexpr (kLeanHop<ST, HOP, MIXHOP, OWN, MIXOWN>) return k_hop_multi_lean<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>;
-    else return k_hop_multi<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>;
+    if constexpr (kLeanHop<ST, HOP, MIXHOP, OWN, MIXOWN>) return k_hop_multi_lean<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS>;
+    else return k_hop_multi<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS>;
 }
+
+static bool warp_sites(int Ns) { return 32 % Ns == 0; }
 
 // ---- launch ------------------------------------------------------------------------------------
 // Sites per CTA: the CTA holds spb * Ns threads, a multiple of 32 and at least 128.
@@ -781,13 +797,16 @@ template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
 struct KernelPick {
     static constexpr bool CAN_STAGE = HOP && ST != ST_DOUBLE;
     // kind: 0 plain single, 1 plain multi, 2 staged single, 3 staged multi
-    static const void* fn(int kind) {
+    static const void* fn(int kind, bool ws) {
         if constexpr (CAN_STAGE) {
             if (kind == 2) return (const void*)k_hop_staged<ST, MIXHOP, OWN, MIXOWN, EPI>;
             if (kind == 3) return (const void*)k_hop_staged_multi<ST, MIXHOP, OWN, MIXOWN, EPI>;
         }
-        return kind == 1 ? (const void*)hop_multi_kernel<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>()
-                         : (const void*)hop_kernel<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>();
+        if (ws)
+            return kind == 1 ? (const void*)hop_multi_kernel<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, true>()
+                             : (const void*)hop_kernel<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, true>();
+        return kind == 1 ? (const void*)hop_multi_kernel<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, false>()
+                         : (const void*)hop_kernel<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, false>();
     }
 };
 
@@ -795,7 +814,7 @@ template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
 static int occupancy(odwf_s* h, int kind, size_t* smem_out) {
     using R = typename Store<ST>::R;
     const int Ns = h->Ns, spb = spb_for(Ns);
-    size_t smem = sizeof(R) * ((size_t)(MIXHOP + MIXOWN) * 2 * Ns * Ns + (size_t)spb * Ns * 24);
+    size_t smem = sizeof(R) * ((size_t)(MIXHOP + MIXOWN) * 2 * Ns * Ns + (size_t)spb * Ns * kRowStride<R>);
     // A-fragment tables of the tensor-core s-mixing (FP32 arithmetic, Ns = 16)
     if (std::is_same<R, float>::value && Ns == 16 && !kLeanHop<ST, HOP, MIXHOP, OWN, MIXOWN>)
         smem += sizeof(uint32_t) * kAfrag16Words * (MIXHOP + MIXOWN);
@@ -804,11 +823,12 @@ static int occupancy(odwf_s* h, int kind, size_t* smem_out) {
     }
     *smem_out = smem;
     static int occ_cache[4][kMaxNs + 1] = {{0}};
-    static bool attr_set[4] = {false, false, false, false};
-    const void* fn = KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::fn(kind);
-    if (!attr_set[kind]) {
+    static bool attr_set[4][2] = {{false, false}, {false, false}, {false, false}, {false, false}};
+    const bool ws = warp_sites(Ns);
+    const void* fn = KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::fn(kind, ws);
+    if (!attr_set[kind][ws]) {
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set[kind] = true;
+        attr_set[kind][ws] = true;
     }
     int& occ = occ_cache[kind][Ns];
     if (occ == 0) {
@@ -840,7 +860,10 @@ static int launch_multi_one(odwf_s* h, const HopArgs* dev_args, int n, int max_v
             return cuda_check(h, cudaGetLastError(), "k_hop_staged_multi launch");
         }
     }
-    hop_multi_kernel<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>()<<<dim3(gx, n), dim3(h->Ns, spb), smem, st>>>(dev_args);
+    if (warp_sites(h->Ns))
+        hop_multi_kernel<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, true>()<<<dim3(gx, n), dim3(h->Ns, spb), smem, st>>>(dev_args);
+    else
+        hop_multi_kernel<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, false>()<<<dim3(gx, n), dim3(h->Ns, spb), smem, st>>>(dev_args);
     return cuda_check(h, cudaGetLastError(), "k_hop_multi launch");
 }
 
@@ -863,11 +886,16 @@ static int launch_one(odwf_s* h, int parity, HopArgs a, cudaStream_t st) {
     const int key = (stg ? 1000000 : 0) + base_key;
     cudaEvent_t ev0 = nullptr;
     if (h->prof) prof_begin(h, key, st, &ev0);
+    bool plain = true;
     if constexpr (KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::CAN_STAGE) {
-        if (stg) k_hop_staged<ST, MIXHOP, OWN, MIXOWN, EPI><<<grid, dim3(Ns, spb), smem, st>>>(a);
-        else hop_kernel<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>()<<<grid, dim3(Ns, spb), smem, st>>>(a);
-    } else {
-        hop_kernel<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>()<<<grid, dim3(Ns, spb), smem, st>>>(a);
+        if (stg) {
+            k_hop_staged<ST, MIXHOP, OWN, MIXOWN, EPI><<<grid, dim3(Ns, spb), smem, st>>>(a);
+            plain = false;
+        }
+    }
+    if (plain) {
+        if (warp_sites(Ns)) hop_kernel<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, true>()<<<grid, dim3(Ns, spb), smem, st>>>(a);
+        else hop_kernel<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, false>()<<<grid, dim3(Ns, spb), smem, st>>>(a);
     }
     if (h->prof) prof_end(h, key, st, ev0);
     return cuda_check(h, cudaGetLastError(), "k_hop launch");
