@@ -135,9 +135,13 @@ def alg_bytes(key, Vh, Ns):
         kind, k = (key // 100) % 10, key % 100
         fld = Vh * Ns * 96
         return {1: (k + 2) * fld, 2: 0, 3: (2 * k + 8) * fld}[kind]
-    if key >= 2000000:  # learned-preconditioner layer: cin inputs, cout outputs, optional own field, FP32
-        cin, cout, own = (key // 100) % 10, (key // 10) % 10, key % 10
-        return Vh * Ns * 96 * (cin + cout + own) + Vh * 8 * 18 * 4
+    if key >= 2000000:  # learned-preconditioner layer: cin inputs, cout outputs, optional own field
+        bf16, cin, cout, own = (key // 1000) % 10, (key // 100) % 10, (key // 10) % 10, key % 10
+        # FP32 fields of 96 bytes per 5D half-site; with BF16 intermediates the 1 -> 2 layer writes and
+        # the 2 -> 1 layer reads 48-byte BF16 rows per channel
+        fin = 48 if (bf16 and cin == 2) else 96
+        fout = 48 if (bf16 and cout == 2) else 96
+        return Vh * Ns * (fin * cin + fout * cout + 96 * own) + Vh * 8 * 18 * 4
     st = (key // 100000) % 10
     hop, mixhop, own, mixown, epi = (key // 10000) % 10, (key // 1000) % 10, (key // 100) % 10, (key // 10) % 10, key % 10
     rb = {0: 8, 1: 4, 2: 2}[st]        # bytes per real of the spinor storage
@@ -172,7 +176,8 @@ def kernel_name(key):
         kind, k = (key // 100) % 10, key % 100
         return {1: f"k_gcr_dots<{k}>", 2: "k_gcr_sum", 3: f"k_gcr_update<{k}>"}[kind]
     if key >= 2000000:
-        return f"k_net_layer<cin={(key // 100) % 10},cout={(key // 10) % 10}{',own' if key % 10 else ''}>"
+        bf = ",bf16" if (key // 1000) % 10 else ""
+        return f"k_net_layer<cin={(key // 100) % 10},cout={(key // 10) % 10}{',own' if key % 10 else ''}{bf}>"
     st = ["fp64", "fp32", "fp16"][(key // 100000) % 10]
     staged = "staged," if key >= 1000000 else ""
     hop, mixhop, own, mixown, epi = (key // 10000) % 10, (key // 1000) % 10, (key // 100) % 10, (key // 10) % 10, key % 10
@@ -443,6 +448,30 @@ def main():
                                  "iters": [s_["iters"] for s_ in stu]}
         for lz in lats_u[:2]:
             lz.close()
+    if not args.quick and DIMS == (16, 16, 16, 32):
+        # the paper's lattice shape, 24^3 x 48 with Ns = 16 (Section 3): every FP32 half field is
+        # 510 MB, far beyond L2, so these per-kernel figures carry no cache effects
+        D24 = (24, 24, 24, 48)
+        l24 = ODWF(D24, NS, M0, om)
+        l24.set_gauge(torch.from_numpy(inputs.random_su3_links(D24, EPS, inputs.seed_for(2, rank))).to(dev))
+        b24 = torch.from_numpy(inputs.gaussian_spinor5(D24, NS, inputs.seed_for(2, 100 + rank))).to(dev)
+        l24.solve(b24, MASS, MASS, opts=opts)
+        l24.profile(True)
+        (_, st24), t24 = timed(lambda: l24.solve(b24, MASS, MASS, opts=opts))
+        p24 = l24.profile_read()
+        l24.profile(False)
+        Vh24 = D24[0] * D24[1] * D24[2] * D24[3] // 2
+        k24 = []
+        for key, (n, ms) in sorted(p24.items(), key=lambda kv: -kv[1][1]):
+            avg_s = ms / 1e3 / n
+            k24.append({"kernel": kernel_name(key), "launches": n, "avg_us": avg_s * 1e6,
+                        "gbs": alg_bytes(key, Vh24, NS) / avg_s / 1e9, "share_ms": ms})
+        extra["paper_lattice"] = {"dims": list(D24), "Ns": NS, "method": f"CGNE, inner {args.prec}, FP64 reliable updates",
+                                  "seconds": t24, "iters": st24["iters"], "true_residual": st24["true_residual"],
+                                  "gflops": st24["iters"] * Vh24 * NS * CG_ITER_FLOPS / t24 / 1e9,
+                                  "kernels": [k for k in k24 if k["share_ms"] > 0.01 * t24 * 1e3]}
+        l24.close()
+        del b24
     if not args.quick:
         # preconditioned solve with the untrained (Neumann-series) network, and, when the timed method
         # is plain CGNE, with a trained one

@@ -192,6 +192,40 @@ __device__ __forceinline__ void s_mix(const R* mt, const R* sh_site, int s, int 
     for (int k = 0; k < 24; ++k) out[k] = accumulate ? out[k] + acc[k] : acc[k];
 }
 
+// As s_mix, with the two chiralities' transposed matrices interleaved, mp[2 (s' Ns + s)] = M_+[s][s']
+// and mp[2 (s' Ns + s) + 1] = M_-[s][s'], so that one 8- (FP32) or 16-byte (FP64) load per s' fetches
+// both coefficients.
+__device__ __forceinline__ void coef_pair(const float* mp, int i, float& cp, float& cm) {
+    const float2 c = reinterpret_cast<const float2*>(mp)[i];
+    cp = c.x, cm = c.y;
+}
+__device__ __forceinline__ void coef_pair(const double* mp, int i, double& cp, double& cm) {
+    const double2 c = reinterpret_cast<const double2*>(mp)[i];
+    cp = c.x, cm = c.y;
+}
+template <typename R>
+__device__ __forceinline__ void s_mix2(const R* mp, const R* sh_site, int s, int Ns, R* out, bool accumulate,
+                                       int rs) {
+    R acc[24];
+#pragma unroll
+    for (int k = 0; k < 24; ++k) acc[k] = 0;
+    for (int sp = 0; sp < Ns; ++sp) {
+        R cp, cm;
+        coef_pair(mp, sp * Ns + s, cp, cm);
+        const R* w = sh_site + sp * rs;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            R t[4];
+            row4_load(w + 4 * q, t);
+            const R c = q < 3 ? cp : cm;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[4 * q + i] = fma(c, t[i], acc[4 * q + i]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 24; ++k) out[k] = accumulate ? out[k] + acc[k] : acc[k];
+}
+
 // ---- fifth-dimension mixing on the tensor cores, Ns = 16 -----------------------------------------
 // With Ns = 16 a warp holds exactly two sites (its own 32 (site, s) threads), so the mixing of those
 // two sites is warp-local: per chirality c the product D = A_c B of the 16 x 16 matrix A_c with the

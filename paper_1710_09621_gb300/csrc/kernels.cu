@@ -292,6 +292,7 @@ __device__ __forceinline__ void hop_body(const HopArgs& a) {
     // staging row stride: 24 reals for the tensor-core mixing (its fragment loads are laid out for
     // it), the padded stride for the FMA mixing
     const int rst = tc ? 24 : kRowStride<R>;
+    const int sst = Ns * rst;
     uint32_t* afr_h = reinterpret_cast<uint32_t*>(smem_raw);
     uint32_t* afr_o = afr_h + (tc && MIXHOP ? kAfrag16Words : 0);
     R* mh = reinterpret_cast<R*>(afr_o + (tc && MIXOWN ? kAfrag16Words : 0));
@@ -304,8 +305,10 @@ __device__ __forceinline__ void hop_body(const HopArgs& a) {
         if (((volatile CGState*)a.state)->flag != FLAG_RUN) return;
     }
     for (int i = tid; i < 2 * Ns * Ns; i += nth) {
-        if (MIXHOP) mh[i] = (R)a.mhop[i];
-        if (MIXOWN) mo[i] = (R)a.mown[i];
+        // interleaved chirality pairs: (M_+, M_-)[s' Ns + s] side by side, one load per s'
+        const int j = i < Ns * Ns ? 2 * i : 2 * (i - Ns * Ns) + 1;
+        if (MIXHOP) mh[j] = (R)a.mhop[i];
+        if (MIXOWN) mo[j] = (R)a.mown[i];
     }
     if constexpr (kTC) {
         if (tc) {
@@ -356,18 +359,18 @@ __device__ __forceinline__ void hop_body(const HopArgs& a) {
             }
         }
         if (MIXHOP) {
-            row24_store(sh + (ls * Ns + s) * rst, v);
+            row24_store(sh + ls * sst + s * rst, v);
             if constexpr (kTC) {
                 if (tc) {
                     __syncwarp();
                     s_mix16_tc(afr_h, sh, lane, warp, ls * Ns + s, v, false);
                 } else {
                     site_barrier<WS>();
-                    s_mix(mh, sh + ls * Ns * rst, s, Ns, v, false, rst);
+                    s_mix2(mh, sh + ls * sst, s, Ns, v, false, rst);
                 }
             } else {
                 site_barrier<WS>();
-                s_mix(mh, sh + ls * Ns * rst, s, Ns, v, false, rst);
+                s_mix2(mh, sh + ls * sst, s, Ns, v, false, rst);
             }
         }
         if (MIXOWN) {
@@ -375,18 +378,18 @@ __device__ __forceinline__ void hop_body(const HopArgs& a) {
                 if (tc) __syncwarp();
                 else site_barrier<WS>();
             }
-            row24_store(sh + (ls * Ns + s) * rst, ow);
+            row24_store(sh + ls * sst + s * rst, ow);
             if constexpr (kTC) {
                 if (tc) {
                     __syncwarp();
                     s_mix16_tc(afr_o, sh, lane, warp, ls * Ns + s, v, true);
                 } else {
                     site_barrier<WS>();
-                    s_mix(mo, sh + ls * Ns * rst, s, Ns, v, true, rst);
+                    s_mix2(mo, sh + ls * sst, s, Ns, v, true, rst);
                 }
             } else {
                 site_barrier<WS>();
-                s_mix(mo, sh + ls * Ns * rst, s, Ns, v, true, rst);
+                s_mix2(mo, sh + ls * sst, s, Ns, v, true, rst);
             }
         }
         if (g5out) g5_flip(v);

@@ -32,8 +32,12 @@ bool coef_host(const odwf_s* h, double m1, double m2, std::vector<double>& host,
 constexpr int kMaxC = 2;          // hidden channels
 constexpr int kXStride = 24;      // bf16 per A-operand row in shared memory (16 used, padded)
 
+// Inference intermediates: the two-channel output of the first layer is stored as BF16 rows, per
+// (cb, colour c, s) one 16-byte chunk [re spins 0..3 | im spins 0..3] at ((cb 3 + c) Ns + s), which is
+// exactly the A-operand row the second layer feeds to the tensor cores (it rounds its inputs to BF16
+// there anyway, so the result is bit-identical to FP32 intermediates at half the bytes).
 struct NetLayerArgs {
-    const float* in[kMaxC];  // input channels, FP32 chunk layout, parity opposite to the output
+    const float* in[kMaxC];  // input channels (FP32 chunk layout, or BF16 rows), opposite parity
     int cin, cout;
     const float* B;          // B operand, FP32 [cin*4 k-tiles][16][8*cout]
     const float* own;        // optional own-parity field for the W0 term
@@ -84,7 +88,7 @@ __device__ __forceinline__ void transport4(const float* in, const float* links, 
         }
 }
 
-template <int CIN, int COUT>
+template <int CIN, int COUT, bool OUTB>
 __global__ void __launch_bounds__(256) k_net_layer(NetLayerArgs a) {
     extern __shared__ __align__(16) unsigned char smem_net[];
     const int Ns = a.Ns;
@@ -240,7 +244,22 @@ __global__ void __launch_bounds__(256) k_net_layer(NetLayerArgs a) {
             if (!a.own_in_mix && co == 0)
 #pragma unroll
                 for (int k = 0; k < 24; ++k) v[k] += wown[k];
-            if (valid) Store<ST_FLOAT>::store(a.out[co], nullptr, (size_t)cb, s, Ns, v);
+            if (valid) {
+                if constexpr (OUTB) {
+                    uint4* o = reinterpret_cast<uint4*>(a.out[co]) + (size_t)cb * 3 * Ns + s;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        uint4 q;
+                        q.x = pack_bf16(v[(0 * 3 + c) * 2], v[(1 * 3 + c) * 2]);
+                        q.y = pack_bf16(v[(2 * 3 + c) * 2], v[(3 * 3 + c) * 2]);
+                        q.z = pack_bf16(v[(0 * 3 + c) * 2 + 1], v[(1 * 3 + c) * 2 + 1]);
+                        q.w = pack_bf16(v[(2 * 3 + c) * 2 + 1], v[(3 * 3 + c) * 2 + 1]);
+                        o[(size_t)c * Ns] = q;
+                    }
+                } else {
+                    Store<ST_FLOAT>::store(a.out[co], nullptr, (size_t)cb, s, Ns, v);
+                }
+            }
         }
     }
 }
@@ -251,6 +270,7 @@ __global__ void __launch_bounds__(256) k_net_layer(NetLayerArgs a) {
 // tensor-core step (2 channels x 4 spins x re/im) giving phi_d, which then takes one FP32 transport
 // by U_d. That is 8 transports per (site, s) instead of 16. B is direction-major here: k-tile d
 // holds W[c,d] for c = 0, 1 (rows c * 8 + spin (re), c * 8 + 4 + spin (im)).
+template <bool INB>
 __global__ void __launch_bounds__(256) k_net_layer_mt(NetLayerArgs a) {
     extern __shared__ __align__(16) unsigned char smem_net[];
     const int Ns = a.Ns;
@@ -297,19 +317,29 @@ __global__ void __launch_bounds__(256) k_net_layer_mt(NetLayerArgs a) {
             // rows (this thread's 3 colours): [v_0 re s0..3 | v_0 im | v_1 re | v_1 im] as BF16
 #pragma unroll
             for (int ci = 0; ci < 2; ++ci) {
-                float x[24];
-                if (valid) Store<ST_FLOAT>::load(a.in[ci], nullptr, (size_t)n, s, Ns, x);
-                else
+                if constexpr (INB) {
+                    // BF16 rows of the first layer: copied to the A-operand rows as they are
+                    const uint4* ip = reinterpret_cast<const uint4*>(a.in[ci]) + (size_t)n * 3 * Ns + s;
 #pragma unroll
-                    for (int k = 0; k < 24; ++k) x[k] = 0.f;
+                    for (int c = 0; c < 3; ++c) {
+                        const uint4 q = valid ? __ldg(ip + (size_t)c * Ns) : make_uint4(0u, 0u, 0u, 0u);
+                        *reinterpret_cast<uint4*>(X + (size_t)(tid * 3 + c) * kXStride + ci * 8) = q;
+                    }
+                } else {
+                    float x[24];
+                    if (valid) Store<ST_FLOAT>::load(a.in[ci], nullptr, (size_t)n, s, Ns, x);
+                    else
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    uint4 q;
-                    q.x = pack_bf16(x[(0 * 3 + c) * 2], x[(1 * 3 + c) * 2]);
-                    q.y = pack_bf16(x[(2 * 3 + c) * 2], x[(3 * 3 + c) * 2]);
-                    q.z = pack_bf16(x[(0 * 3 + c) * 2 + 1], x[(1 * 3 + c) * 2 + 1]);
-                    q.w = pack_bf16(x[(2 * 3 + c) * 2 + 1], x[(3 * 3 + c) * 2 + 1]);
-                    *reinterpret_cast<uint4*>(X + (size_t)(tid * 3 + c) * kXStride + ci * 8) = q;
+                        for (int k = 0; k < 24; ++k) x[k] = 0.f;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        uint4 q;
+                        q.x = pack_bf16(x[(0 * 3 + c) * 2], x[(1 * 3 + c) * 2]);
+                        q.y = pack_bf16(x[(2 * 3 + c) * 2], x[(3 * 3 + c) * 2]);
+                        q.z = pack_bf16(x[(0 * 3 + c) * 2 + 1], x[(1 * 3 + c) * 2 + 1]);
+                        q.w = pack_bf16(x[(2 * 3 + c) * 2 + 1], x[(3 * 3 + c) * 2 + 1]);
+                        *reinterpret_cast<uint4*>(X + (size_t)(tid * 3 + c) * kXStride + ci * 8) = q;
+                    }
                 }
             }
             __syncwarp();
@@ -670,8 +700,10 @@ size_t layer_smem(const odwf_s* h, int cout) {
 }
 
 // one layer; `parity` is the output parity
+// `bf16`: inference intermediates (the 1 -> 2 layer writes, the 2 -> 1 layer reads BF16 rows)
 int net_layer(odwf_net_s* n, int parity, int cin, int cout, const float* const* in, const float* B, const float* own,
-              const float* w0, int own_in_mix, float* const* out, const double* mix, float c_hop, cudaStream_t st) {
+              const float* w0, int own_in_mix, float* const* out, const double* mix, float c_hop, cudaStream_t st,
+              int bf16 = 0) {
     odwf_s* h = n->h;
     NetLayerArgs a{};
     for (int i = 0; i < cin; ++i) a.in[i] = in[i];
@@ -691,24 +723,25 @@ int net_layer(odwf_net_s* n, int parity, int cin, int cout, const float* const* 
     const int spb = spb_for(h->Ns);
     const size_t smem = layer_smem(h, cout);
     const dim3 blk(h->Ns, spb);
-    auto launch = [&](auto fn) -> int {
-        static bool set = false;
-        if (!set) {
+    auto launch = [&](void (*fn)(NetLayerArgs), int kind) -> int {
+        // every layer kernel has the same type: one attribute flag per kernel, not per type
+        static bool set[6] = {false, false, false, false, false, false};
+        if (!set[kind]) {
             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            set = true;
+            set[kind] = true;
         }
         int occ = 1;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, h->Ns * spb, smem);
-        const int key = 2000000 + cin * 100 + cout * 10 + (own ? 1 : 0);
+        const int key = 2000000 + (bf16 ? 1000 : 0) + cin * 100 + cout * 10 + (own ? 1 : 0);
         cudaEvent_t ev0 = nullptr;
         if (h->prof) prof_begin(h, key, st, &ev0);
         fn<<<grid_for_groups(h, occ < 1 ? 1 : occ), blk, smem, st>>>(a);
         if (h->prof) prof_end(h, key, st, ev0);
         return cuda_check(h, cudaGetLastError(), "k_net_layer");
     };
-    if (cin == 1 && cout == 2) return launch(k_net_layer<1, 2>);
-    if (cin == 2 && cout == 1) return launch(k_net_layer_mt);
-    if (cin == 1 && cout == 1) return launch(k_net_layer<1, 1>);
+    if (cin == 1 && cout == 2) return bf16 ? launch(k_net_layer<1, 2, true>, 0) : launch(k_net_layer<1, 2, false>, 1);
+    if (cin == 2 && cout == 1) return bf16 ? launch(k_net_layer_mt<true>, 2) : launch(k_net_layer_mt<false>, 3);
+    if (cin == 1 && cout == 1) return launch(k_net_layer<1, 1, false>, 4);
     return net_err(n, ODWF_EINVAL, "unsupported layer shape");
 }
 
@@ -726,21 +759,23 @@ int net_apply_even(odwf_net_s* n, const float* r, float* outp, int adjoint, cuda
     int rc = net_prep(n, st);
     if (rc) return rc;
     float* v[2] = {n->f[1], n->f[2]};
+    // two channels: BF16 intermediates between the layers (one channel keeps the FP32 path)
+    const int bf = n->C == 2 ? 1 : 0;
     if (!adjoint) {
         if ((rc = net_smix(n, r, n->f[0], Ainv, st))) return rc;
         const float* in1[1] = {n->f[0]};
-        if ((rc = net_layer(n, 1, 1, n->C, in1, n->B0, nullptr, nullptr, 0, v, Ainv, 1.f, st))) return rc;
+        if ((rc = net_layer(n, 1, 1, n->C, in1, n->B0, nullptr, nullptr, 0, v, Ainv, 1.f, st, bf))) return rc;
         const float* in2[2] = {v[0], v[1]};
         float* o[1] = {outp};
-        return net_layer(n, 0, n->C, 1, in2, n->B1, n->f[0], n->w0f, 0, o, Ainv, 0.25f, st);
+        return net_layer(n, 0, n->C, 1, in2, n->B1, n->f[0], n->w0f, 0, o, Ainv, 0.25f, st, bf);
     }
     // M^dag g = A^{-T} [ W0^dag g + sum T^dag W1^dag A^{-T} sum T^dag (W2^dag / 4) A^{-T} g ]
     if ((rc = net_smix(n, r, n->f[0], AinvT, st))) return rc;  // gy * 4
     const float* in1[1] = {n->f[0]};
-    if ((rc = net_layer(n, 1, 1, n->C, in1, n->B2, nullptr, nullptr, 0, v, AinvT, 1.f, st))) return rc;
+    if ((rc = net_layer(n, 1, 1, n->C, in1, n->B2, nullptr, nullptr, 0, v, AinvT, 1.f, st, bf))) return rc;
     const float* in2[2] = {v[0], v[1]};
     float* o[1] = {outp};
-    return net_layer(n, 0, n->C, 1, in2, n->B3, r, n->w0adj, 1, o, AinvT, 1.f, st);
+    return net_layer(n, 0, n->C, 1, in2, n->B3, r, n->w0adj, 1, o, AinvT, 1.f, st, bf);
 }
 
 int wgrad(odwf_net_s* n, int parity, int cin, int cout, int identity, const float* const* in, const float* const* dl,
