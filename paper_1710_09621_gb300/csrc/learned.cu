@@ -88,6 +88,18 @@ __device__ __forceinline__ void transport4(const float* in, const float* links, 
         }
 }
 
+// The group's links (spb sites x 8 directions x 20 floats), staged once per group by the whole CTA;
+// zeros past the last site. The caller synchronises the CTA afterwards.
+__device__ __forceinline__ void stage_group_links(const float* links, float* lk, int g, int spb, int Vh, int tid,
+                                                  int nth) {
+    const float4* src = reinterpret_cast<const float4*>(links);
+    float4* dst = reinterpret_cast<float4*>(lk);
+    for (int i = tid; i < spb * 8 * 5; i += nth) {
+        const int c_ = g * spb + i / 40;
+        dst[i] = c_ < Vh ? __ldg(src + (size_t)c_ * 40 + i % 40) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
 template <int CIN, int COUT, bool OUTB>
 __global__ void __launch_bounds__(256) k_net_layer(NetLayerArgs a) {
     extern __shared__ __align__(16) unsigned char smem_net[];
@@ -270,6 +282,12 @@ __global__ void __launch_bounds__(256) k_net_layer(NetLayerArgs a) {
 // tensor-core step (2 channels x 4 spins x re/im) giving phi_d, which then takes one FP32 transport
 // by U_d. That is 8 transports per (site, s) instead of 16. B is direction-major here: k-tile d
 // holds W[c,d] for c = 0, 1 (rows c * 8 + spin (re), c * 8 + 4 + spin (im)).
+// The transport runs where the mma leaves phi_d: the A rows are ordered colour-major within a warp
+// (row 96 warp + 32 colour + lane) and the B columns as (spin, re/im) pairs, so the D fragment of
+// lane (gid, tig) in m-tile (colour c, half h) is phi_d(thread 16 h + gid [+ 8], colour c, spin tig)
+// as one complex number. Each lane therefore holds all three colours of one spin for four threads
+// of its warp, applies U_d to them and keeps the sums in registers across the eight directions; one
+// shared-memory transpose per site group (not one per direction) hands every thread its own spinor.
 template <bool INB>
 __global__ void __launch_bounds__(256) k_net_layer_mt(NetLayerArgs a) {
     extern __shared__ __align__(16) unsigned char smem_net[];
@@ -278,43 +296,58 @@ __global__ void __launch_bounds__(256) k_net_layer_mt(NetLayerArgs a) {
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
     const int lane = tid & 31, warp = tid >> 5;
     const int gid = lane >> 2, tig = lane & 3;
-    // shared memory as k_net_layer<2, 1>: [mix][X rows * kXStride bf16][Y rows * 9 floats]; sh reuses X
+    // shared memory: [mix][X rows * kXStride bf16][links of the group's sites, spb x 8 x 20 floats]
+    // [s-mixing fragment table]; sh (rows of 24 floats, the transpose and the s-mixing) reuses X
     float* mix = reinterpret_cast<float*>(smem_net);
     __nv_bfloat16* X = reinterpret_cast<__nv_bfloat16*>(mix + 2 * Ns * Ns);
     const int rows = nth * 3;
-    float* Y = reinterpret_cast<float*>(X + (size_t)rows * kXStride);
     float* sh = reinterpret_cast<float*>(X);
-    // Ns = 16: warp-local tensor-core s-mixing with its A-fragment table after Y
+    float* lk = reinterpret_cast<float*>(X + (size_t)rows * kXStride);
+    // Ns = 16: warp-local tensor-core s-mixing with its A-fragment table after the links
     const bool tc = Ns == 16;
-    uint32_t* afr = reinterpret_cast<uint32_t*>(Y + (size_t)rows * 9 * 1);
+    uint32_t* afr = reinterpret_cast<uint32_t*>(lk + (size_t)spb * 8 * 20);
     if (a.mix) {
         for (int i = tid; i < 2 * Ns * Ns; i += nth) mix[i] = (float)a.mix[i];
         if (tc) s_mix16_afrag(a.mix, afr, tid, nth);
     }
+    // B columns in (spin, re/im) order: fragment column n = 2 spin + re/im is stored column
+    // (re/im) 4 + spin
     uint32_t bfrag[8][2];
+    const int bcol = (gid & 1) * 4 + (gid >> 1);
 #pragma unroll
     for (int d = 0; d < 8; ++d) {
         const float* Bt = a.B + (size_t)d * 16 * 8;
-        bfrag[d][0] = pack_bf16(Bt[(2 * tig) * 8 + gid], Bt[(2 * tig + 1) * 8 + gid]);
-        bfrag[d][1] = pack_bf16(Bt[(2 * tig + 8) * 8 + gid], Bt[(2 * tig + 9) * 8 + gid]);
+        bfrag[d][0] = pack_bf16(Bt[(2 * tig) * 8 + bcol], Bt[(2 * tig + 1) * 8 + bcol]);
+        bfrag[d][1] = pack_bf16(Bt[(2 * tig + 8) * 8 + bcol], Bt[(2 * tig + 9) * 8 + bcol]);
     }
-    float w0[32];
-    if (a.w0)
-#pragma unroll
-        for (int k = 0; k < 32; ++k) w0[k] = a.w0[k];
     __syncthreads();
 
     for (int g = blockIdx.x; g * spb < a.Vh; g += gridDim.x) {
         __syncthreads();
         const int cb = g * spb + ls;
         const bool valid = cb < a.Vh;
-        float v[24];
+        // this lane's sums: acc[h][e][colour][re, im] of spin tig for thread 16 h + gid + 8 e
+        float acc[2][2][3][2];
 #pragma unroll
-        for (int k = 0; k < 24; ++k) v[k] = 0.f;
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) acc[h][e][i][0] = acc[h][e][i][1] = 0.f;
+        // the group's links, all eight directions, staged once
+        stage_group_links(a.links, lk, g, spb, a.Vh, tid, nth);
+        __syncthreads();
+        // site (within the group) of each thread this lane serves
+        int lsite[2][2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) lsite[h][e] = (warp * 32 + 16 * h + gid + 8 * e) / Ns;
 #pragma unroll 1
         for (int d = 0; d < 8; ++d) {
             const int n = valid ? __ldg(a.nbr + (size_t)cb * 8 + d) : 0;
-            // rows (this thread's 3 colours): [v_0 re s0..3 | v_0 im | v_1 re | v_1 im] as BF16
+            // A rows of this thread, colour-major: row 96 warp + 32 c + lane holds
+            // [v_0 re s0..3 | v_0 im | v_1 re | v_1 im] of colour c as BF16
 #pragma unroll
             for (int ci = 0; ci < 2; ++ci) {
                 if constexpr (INB) {
@@ -323,7 +356,7 @@ __global__ void __launch_bounds__(256) k_net_layer_mt(NetLayerArgs a) {
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const uint4 q = valid ? __ldg(ip + (size_t)c * Ns) : make_uint4(0u, 0u, 0u, 0u);
-                        *reinterpret_cast<uint4*>(X + (size_t)(tid * 3 + c) * kXStride + ci * 8) = q;
+                        *reinterpret_cast<uint4*>(X + (size_t)(warp * 96 + c * 32 + lane) * kXStride + ci * 8) = q;
                     }
                 } else {
                     float x[24];
@@ -338,56 +371,69 @@ __global__ void __launch_bounds__(256) k_net_layer_mt(NetLayerArgs a) {
                         q.y = pack_bf16(x[(2 * 3 + c) * 2], x[(3 * 3 + c) * 2]);
                         q.z = pack_bf16(x[(0 * 3 + c) * 2 + 1], x[(1 * 3 + c) * 2 + 1]);
                         q.w = pack_bf16(x[(2 * 3 + c) * 2 + 1], x[(3 * 3 + c) * 2 + 1]);
-                        *reinterpret_cast<uint4*>(X + (size_t)(tid * 3 + c) * kXStride + ci * 8) = q;
+                        *reinterpret_cast<uint4*>(X + (size_t)(warp * 96 + c * 32 + lane) * kXStride + ci * 8) = q;
                     }
                 }
             }
             __syncwarp();
-            // phi_d rows = X rows W_d (one k16 step, one n8 tile), to Y (warp-private rows)
 #pragma unroll
-            for (int m = 0; m < 6; ++m) {
-                const int r0 = warp * 96 + m * 16;
-                const uint32_t* x0 = reinterpret_cast<const uint32_t*>(X + (size_t)(r0 + gid) * kXStride);
-                const uint32_t* x8 = reinterpret_cast<const uint32_t*>(X + (size_t)(r0 + gid + 8) * kXStride);
-                uint32_t af[4] = {x0[tig], x8[tig], x0[tig + 4], x8[tig + 4]};
-                float acc[4] = {0.f, 0.f, 0.f, 0.f};
-                mma_bf16(acc, af, bfrag[d]);
-                // scalar stores: rows of 9 floats are only 4-byte aligned
-                float* y0 = Y + (size_t)(r0 + gid) * 9 + 2 * tig;
-                float* y8 = Y + (size_t)(r0 + gid + 8) * 9 + 2 * tig;
-                y0[0] = acc[0];
-                y0[1] = acc[1];
-                y8[0] = acc[2];
-                y8[1] = acc[3];
-            }
-            __syncwarp();
-            // phi_d of this thread (3 colours x 4 spins), then v += U_d phi_d
-            float phi[24], u[18];
+            for (int h = 0; h < 2; ++h) {
+                // phi_d of the 16 threads 16 h .. 16 h + 15, colours 0..2: D fragments in registers
+                float ph[3][4];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float* yr = Y + (size_t)(tid * 3 + c) * 9;
+                for (int c = 0; c < 3; ++c) {
+                    const int r0 = warp * 96 + c * 32 + 16 * h;
+                    const uint32_t* x0 = reinterpret_cast<const uint32_t*>(X + (size_t)(r0 + gid) * kXStride);
+                    const uint32_t* x8 = reinterpret_cast<const uint32_t*>(X + (size_t)(r0 + gid + 8) * kXStride);
+                    uint32_t af[4] = {x0[tig], x8[tig], x0[tig + 4], x8[tig + 4]};
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    phi[(b * 3 + c) * 2] = yr[b];
-                    phi[(b * 3 + c) * 2 + 1] = yr[4 + b];
+                    for (int q = 0; q < 4; ++q) ph[c][q] = 0.f;
+                    mma_bf16(ph[c], af, bfrag[d]);
                 }
-            }
-            Links<ST_FLOAT>::load(a.links, cb < a.Vh ? cb : 0, d, u);
+                // U_d of each served thread's site applied to (phi colours 0..2) of spin tig
 #pragma unroll
-            for (int sp = 0; sp < 4; ++sp)
+                for (int e = 0; e < 2; ++e) {
+                    float u[20];
+                    {
+                        const float4* lp = reinterpret_cast<const float4*>(lk) + (lsite[h][e] * 8 + d) * 5;
 #pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    float re = v[(sp * 3 + i) * 2], im = v[(sp * 3 + i) * 2 + 1];
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) {
-                        const float ur = u[(i * 3 + j) * 2], ui = u[(i * 3 + j) * 2 + 1];
-                        const float pr = phi[(sp * 3 + j) * 2], pi = phi[(sp * 3 + j) * 2 + 1];
-                        re = fmaf(ur, pr, fmaf(-ui, pi, re));
-                        im = fmaf(ur, pi, fmaf(ui, pr, im));
+                        for (int q = 0; q < 5; ++q) row4_load(reinterpret_cast<const float*>(lp + q), u + 4 * q);
                     }
-                    v[(sp * 3 + i) * 2] = re;
-                    v[(sp * 3 + i) * 2 + 1] = im;
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        float re = acc[h][e][i][0], im = acc[h][e][i][1];
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) {
+                            const float ur = u[(i * 3 + j) * 2], ui = u[(i * 3 + j) * 2 + 1];
+                            const float pr = ph[j][2 * e], pi = ph[j][2 * e + 1];
+                            re = fmaf(ur, pr, fmaf(-ui, pi, re));
+                            im = fmaf(ur, pi, fmaf(ui, pr, im));
+                        }
+                        acc[h][e][i][0] = re;
+                        acc[h][e][i][1] = im;
+                    }
                 }
+            }
+            __syncwarp();  // X rows are rewritten by the next direction
+        }
+        // transpose: every lane writes its sums into the served threads' rows of 24 floats, then each
+        // thread reads its own spinor. The rows (sh) alias other warps' X rows: CTA barrier first.
+        __syncthreads();
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                float* row = sh + (size_t)(warp * 32 + 16 * h + gid + 8 * e) * 24;
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+                    *reinterpret_cast<float2*>(row + (tig * 3 + i) * 2) = make_float2(acc[h][e][i][0], acc[h][e][i][1]);
+            }
+        __syncwarp();
+        float v[24];
+        {
+            const float* row = sh + (size_t)tid * 24;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) row4_load(row + 4 * q, v + 4 * q);
         }
         float ow[24];
         if (a.own && valid) Store<ST_FLOAT>::load(a.own, nullptr, (size_t)cb, s, Ns, ow);
@@ -403,7 +449,7 @@ __global__ void __launch_bounds__(256) k_net_layer_mt(NetLayerArgs a) {
                 if (a.w0) {
 #pragma unroll
                     for (int aa = 0; aa < 4; ++aa) {
-                        const float wr = w0[(b * 4 + aa) * 2], wi = w0[(b * 4 + aa) * 2 + 1];
+                        const float wr = __ldg(a.w0 + (b * 4 + aa) * 2), wi = __ldg(a.w0 + (b * 4 + aa) * 2 + 1);
                         const float xr = ow[(aa * 3 + c) * 2], xi = ow[(aa * 3 + c) * 2 + 1];
                         re = fmaf(wr, xr, fmaf(-wi, xi, re));
                         im = fmaf(wr, xi, fmaf(wi, xr, im));
@@ -693,10 +739,13 @@ int grid_for_groups(odwf_s* h, int occ) {
     return g > groups ? groups : (g < 1 ? 1 : g);
 }
 
+// cout D-fragment row sets, or (cout == 0) the 2 -> 1 layer's layout: no D-fragment rows (its sums
+// stay in registers) and the group's staged links instead; then the s-mixing fragment table
 size_t layer_smem(const odwf_s* h, int cout) {
     const int spb = spb_for(h->Ns), nth = spb * h->Ns, rows = nth * 3;
     return sizeof(float) * 2 * h->Ns * h->Ns + sizeof(__nv_bfloat16) * (size_t)rows * kXStride +
-           sizeof(float) * (size_t)rows * 9 * cout + (h->Ns == 16 ? sizeof(uint32_t) * kAfrag16Words : 0);
+           sizeof(float) * (size_t)rows * 9 * cout + (cout == 0 ? sizeof(float) * (size_t)spb * 8 * 20 : 0) +
+           (h->Ns == 16 ? sizeof(uint32_t) * kAfrag16Words : 0);
 }
 
 // one layer; `parity` is the output parity
@@ -721,7 +770,8 @@ int net_layer(odwf_net_s* n, int parity, int cin, int cout, const float* const* 
     a.Vh = h->Vh;
     a.Ns = h->Ns;
     const int spb = spb_for(h->Ns);
-    const size_t smem = layer_smem(h, cout);
+    // the 2 -> 1 layer keeps its transport sums in registers and needs no D-fragment rows (cout 0)
+    const size_t smem = layer_smem(h, (cin == 2 && cout == 1) ? 0 : cout);
     const dim3 blk(h->Ns, spb);
     auto launch = [&](void (*fn)(NetLayerArgs), int kind) -> int {
         // every layer kernel has the same type: one attribute flag per kernel, not per type
