@@ -64,3 +64,26 @@ def test_mp_term_lists_match_oracle():
     assert key(pp) == key([eofa.term_from_ratio((m, m), (M, m)), eofa.term_from_ratio((M, m), (M, M))])
     with pytest.raises(binding.OdwfError):
         binding.mp_terms(binding.MP_NEW, m, [2.0], M)
+
+
+def test_library_k_matches_the_rank_one_factor():
+    """The library's k(m_j, m_i) (host code) is the coefficient of the rank-one difference
+    R5 (M(m_j) - M(m_i)) = k Omega Omega^T of Eq.(delta_ij), found numerically from the oracle's
+    dense fifth-dimension matrices, and reduces to (1 - m)/(1 + m) for m_j = 1."""
+    import numpy as np
+    from paper_1710_09621_gb300 import binding, build, inputs
+    try:
+        build.build()
+    except RuntimeError as e:
+        pytest.skip(str(e))
+    from oracle import fifth
+    om = inputs.omega_zolotarev(8, 0.05, 6.2)
+    R5 = np.eye(8)[::-1]
+    for mj, mi in ((0.1, 0.01), (1.0, 0.05), (0.3, 0.7)):
+        D = R5 @ (fifth.m_matrix(om, mj, -1) - fifth.m_matrix(om, mi, -1))
+        ev = np.linalg.eigvalsh(0.5 * (D + D.T))
+        lead = ev[np.argmax(np.abs(ev))]          # the single non-zero eigenvalue = k |Omega|^2
+        Om = fifth.omega_vector(om, -1)
+        assert binding.eofa_k(mj, mi) == pytest.approx(lead / (Om @ Om), rel=1e-12)
+    for m in (0.01, 0.1, 0.5):
+        assert binding.eofa_k(1.0, m) == pytest.approx((1 - m) / (1 + m), rel=1e-15)
