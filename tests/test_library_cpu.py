@@ -87,3 +87,32 @@ def test_library_k_matches_the_rank_one_factor():
         assert binding.eofa_k(mj, mi) == pytest.approx(lead / (Om @ Om), rel=1e-12)
     for m in (0.01, 0.1, 0.5):
         assert binding.eofa_k(1.0, m) == pytest.approx((1 - m) / (1 + m), rel=1e-15)
+
+
+def test_create_rejects_bad_arguments_before_touching_the_device():
+    """odwf_create validates its arguments on the host (no GPU needed): odd or too large Ns, odd
+    extents, m0 outside (0, 2), non-positive or non-R5-symmetric omega give ODWF_EINVAL with a
+    message; with valid arguments and no usable GPU it fails loudly (ODWF_ECUDA), never falls back."""
+    import numpy as np
+    from paper_1710_09621_gb300 import binding, build
+    try:
+        build.build()
+    except RuntimeError as e:
+        pytest.skip(str(e))
+    om8 = np.ones(8)
+    bad = [((4, 4, 4, 4), 7, 1.3, np.ones(7), "Ns"),
+           ((4, 4, 4, 4), 34, 1.3, np.ones(34), "Ns"),
+           ((4, 4, 3, 4), 8, 1.3, om8, "even"),
+           ((4, 4, 4, 4), 8, 2.5, om8, "m0"),
+           ((4, 4, 4, 4), 8, 1.3, np.r_[om8[:-1], -1.0], "omega"),
+           ((4, 4, 4, 4), 8, 1.3, np.arange(1.0, 9.0), "R5")]
+    for dims, ns, m0, om, word in bad:
+        with pytest.raises(binding.OdwfError) as ei:
+            binding.ODWF(dims, ns, m0, om)
+        assert ei.value.code == binding.ODWF_EINVAL and word in str(ei.value), (dims, ns, m0, str(ei.value))
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        return
+    with pytest.raises(binding.OdwfError) as ei:
+        binding.ODWF((4, 4, 4, 4), 8, 1.3, om8)
+    assert ei.value.code == binding.ODWF_ECUDA
