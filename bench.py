@@ -54,6 +54,20 @@ def per_solve_seconds(max_elapsed, steps, world):
     return max_elapsed / (steps * world)
 
 
+def average_plaquette(U):
+    """Average plaquette Re tr(U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag) / 3 of a link array
+    [mu][t][z][y][x][3][3] (periodic links): the statistic that characterises a synthetic gauge field."""
+    import numpy as np
+    axis = {0: 3, 1: 2, 2: 1, 3: 0}  # site axis of direction mu within U[mu]
+    tot = 0.0
+    for mu in range(4):
+        for nu in range(mu + 1, 4):
+            a = U[mu] @ np.roll(U[nu], -1, axis=axis[mu])
+            b = U[nu] @ np.roll(U[mu], -1, axis=axis[nu])
+            tot += np.sum(a * b.conj()).real / (3.0 * a[..., 0, 0].size)  # tr(a b^dag)
+    return tot / 6.0
+
+
 def dram_traffic(kernel, dims, ns):
     """ncu-measured DRAM bytes per launch of `kernel` on this lattice, or None if not captured."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
@@ -287,7 +301,10 @@ def main():
     build.build()
     dev = torch.device("cuda", local)
     om = inputs.omega_zolotarev(NS, 0.05, 6.2)
-    U = torch.from_numpy(inputs.random_su3_links(DIMS, EPS, inputs.seed_for(1, rank))).to(dev)
+    U_host = inputs.random_su3_links(DIMS, EPS, inputs.seed_for(1, rank))
+    plaq = average_plaquette(U_host)
+    U = torch.from_numpy(U_host).to(dev)
+    del U_host
     b_host = torch.from_numpy(inputs.gaussian_spinor5(DIMS, NS, inputs.seed_for(1, 100 + rank))).pin_memory()
     b = b_host.to(dev)
     lat = ODWF(DIMS, NS, M0, om)
@@ -455,7 +472,10 @@ def main():
         # 510 MB, far beyond L2, so these per-kernel figures carry no cache effects
         D24 = (24, 24, 24, 48)
         l24 = ODWF(D24, NS, M0, om)
-        l24.set_gauge(torch.from_numpy(inputs.random_su3_links(D24, EPS, inputs.seed_for(2, rank))).to(dev))
+        U24 = inputs.random_su3_links(D24, EPS, inputs.seed_for(2, rank))
+        plaq24 = average_plaquette(U24)
+        l24.set_gauge(torch.from_numpy(U24).to(dev))
+        del U24
         b24 = torch.from_numpy(inputs.gaussian_spinor5(D24, NS, inputs.seed_for(2, 100 + rank))).to(dev)
         l24.solve(b24, MASS, MASS, opts=opts)
         l24.profile(True)
@@ -468,7 +488,8 @@ def main():
             avg_s = ms / 1e3 / n
             k24.append({"kernel": kernel_name(key), "launches": n, "avg_us": avg_s * 1e6,
                         "gbs": alg_bytes(key, Vh24, NS) / avg_s / 1e9, "share_ms": ms})
-        extra["paper_lattice"] = {"dims": list(D24), "Ns": NS, "method": f"CGNE, inner {args.prec}, FP64 reliable updates",
+        extra["paper_lattice"] = {"dims": list(D24), "Ns": NS, "plaquette": plaq24,
+                                  "method": f"CGNE, inner {args.prec}, FP64 reliable updates",
                                   "seconds": t24, "iters": st24["iters"], "true_residual": st24["true_residual"],
                                   "gflops": st24["iters"] * Vh24 * NS * CG_ITER_FLOPS / t24 / 1e9,
                                   "kernels": [k for k in k24 if k["share_ms"] > 0.01 * t24 * 1e3]}
@@ -556,7 +577,8 @@ def main():
                   {"single": "f32 (FP64 reliable updates)", "half": "f16 storage/f32 (FP64 reliable updates)",
                    "double": "f64"}[args.prec]),
         "data": "synthetic",
-        "config": dict(WORKLOAD, prec=args.prec, delta=args.delta, l2="inputs larger than L2 (each solve streams >1 GB)",
+        "config": dict(WORKLOAD, prec=args.prec, delta=args.delta, plaquette=plaq,
+                       l2="inputs larger than L2 (each solve streams >1 GB)",
                        parallelism=f"replicas x{world}"),
         "solve": {"iters": stats[-1]["iters"], "reliable_updates": stats[-1]["reliable_updates"],
                   "true_residual": max(s["true_residual"] for s in stats),

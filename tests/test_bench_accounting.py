@@ -58,3 +58,23 @@ def test_traffic_table_entries_name_measured_kernels():
 def test_names_round_trip_to_known_kernels(key):
     assert bench.kernel_name(key).startswith("k_")
     assert bench.alg_bytes(key, VH, NS) >= 0
+
+
+def test_average_plaquette():
+    """bench.py's plaquette: 1 on unit links, gauge invariant, and equal to the oracle's on a seeded
+    field (written independently there)."""
+    import numpy as np
+    from oracle import wilson
+    from paper_1710_09621_gb300 import inputs
+    dims = (4, 2, 2, 4)
+    U1 = np.broadcast_to(np.eye(3, dtype=np.complex128), (4, dims[3], dims[2], dims[1], dims[0], 3, 3)).copy()
+    assert bench.average_plaquette(U1) == pytest.approx(1.0, abs=1e-15)
+    U = inputs.random_su3_links(dims, 0.3, 7)
+    p = bench.average_plaquette(U)
+    assert p == pytest.approx(wilson.plaquette(U), abs=1e-14)
+    assert 0.0 < p < 1.0
+    # U_mu(x) -> G(x) U_mu(x) G(x + mu)^dag leaves it unchanged
+    G = inputs.random_su3_links(dims, 1.0, 8)[0]
+    axis = {0: 3, 1: 2, 2: 1, 3: 0}
+    Ug = np.stack([G @ U[mu] @ np.roll(G, -1, axis=axis[mu]).conj().swapaxes(-1, -2) for mu in range(4)])
+    assert bench.average_plaquette(Ug) == pytest.approx(p, abs=1e-13)
