@@ -102,9 +102,10 @@ const char* odwf_last_error(const odwf_t* h);
  * the stream reaches this point. Must be called before any operator, solve or EOFA call. */
 int odwf_set_gauge(odwf_t* h, const void* U, void* stream);
 
-/* out = Op(m1, m2) in, or its adjoint, on full 5D fields (device, complex128, ABI layout).
- * op: ODWF_OP_*. prec: ODWF_PREC_DOUBLE or ODWF_PREC_SINGLE (arithmetic of the hopping and
- * fifth-dimension kernels; in/out stay FP64). in and out must not overlap. */
+/* out = Op(m1, m2) in, or its adjoint, on full 5D fields (device, complex128, ABI layout): D_T of
+ * Eq.(DTm1m2), H_T = gamma_5 R5 D_T (after Eq.(m1m2_m3m2)) or D_odwf (Eq.(detDodwf)), see ODWF_OP_*.
+ * prec: ODWF_PREC_DOUBLE or ODWF_PREC_SINGLE (arithmetic of the hopping and fifth-dimension
+ * kernels; in/out stay FP64). in and out must not overlap. */
 int odwf_apply(odwf_t* h, int op, double m1, double m2, const void* in, void* out, int prec, void* stream);
 int odwf_apply_dag(odwf_t* h, int op, double m1, double m2, const void* in, void* out, int prec, void* stream);
 
@@ -143,8 +144,10 @@ int eofa_solve_batch(odwf_t* h, int n, const double* m12, const void* const* b, 
 int eofa_solve_multi(odwf_t* const* hs, int n, const double* m12, const void* const* b, void* const* x,
                      const odwf_solve_opts* opts, odwf_solve_stats* stats, void* stream);
 
-/* S = phi^dag X phi for one term (phi: 4D device field; only the term's chirality is read).
- * Written to *S_host. stats (may be NULL) receives the solve's statistics. */
+/* S = phi^dag X phi for one term, X the 4D operator of Eq.(m1m2_m1m4) (chirality -) or
+ * Eq.(m1m2_m3m2) (chirality +): X = 1 -/+ k Omega^T H_T(m3, m4)^{-1} Omega on the term's chirality,
+ * one H_T solve. phi: 4D device field (only the term's chirality is read). Written to *S_host.
+ * stats (may be NULL) receives the solve's statistics. Synchronises `stream`. */
 int eofa_action(odwf_t* h, const eofa_term* term, const void* phi, double* S_host,
                 const odwf_solve_opts* opts, odwf_solve_stats* stats, void* stream);
 
@@ -211,11 +214,15 @@ int eofa_solve_gcr(odwf_t* h, odwf_net_t* net, double m1, double m2, const void*
  * solver state; call it between solves. */
 int odwf_autotune(odwf_t* h, int prec, char* report, int report_len, void* stream);
 
-/* Kernel timing for measurement: while enabled, every launch of the fused hopping kernels is
- * bracketed by CUDA events on its stream. odwf_profile_read synchronises the device and returns,
- * per kernel variant seen since the last enable, its key (storage*100000 + hop*10000 +
- * mixhop*1000 + own*100 + mixown*10 + epilogue), the number of launches and the summed event time
- * in milliseconds; n_io is the capacity of the arrays on entry and the number of variants on exit.
+/* Kernel timing for measurement: while enabled, every launch of the library's kernels on this
+ * handle (hopping, network, GCR, layout and vector kernels) is bracketed by CUDA events on its
+ * stream. odwf_profile_read synchronises the device and returns, per kernel variant seen since the
+ * last enable, its key, the number of launches and the summed event time in milliseconds; n_io is
+ * the capacity of the arrays on entry and the number of variants on exit. Keys: hopping kernels
+ * storage*100000 + hop*10000 + mixhop*1000 + own*100 + mixown*10 + epilogue (+1000000 for the
+ * bulk-staged gathers); network layers 2000000 + bf16*1000 + cin*100 + cout*10 + own; GCR kernels
+ * 3000000 + kind*100 + basis size; layout / vector kernels 4000000 + kind*100 + storage*10 +
+ * storage (kind 1 pack, 2 unpack, 3 convert, 4 axpy to FP64, 5 norm).
  * The paper has no counterpart: this is instrumentation. */
 int odwf_profile_enable(odwf_t* h, int enable);
 int odwf_profile_read(odwf_t* h, int* keys, int* launches, double* total_ms, int* n_io);
