@@ -42,6 +42,10 @@ extern "C" {
 #define ODWF_ENOCONV    -4   /* the solver reached maxiter without meeting the tolerance      */
 #define ODWF_EBREAKDOWN -5   /* Krylov breakdown: <p,p> <= 0 or a NaN/Inf in a reduction      */
 #define ODWF_ETIMEOUT   -6   /* the solver exceeded its wall-clock budget                     */
+#define ODWF_EFAULT     -7   /* a kernel's bounded wait for its bulk copies ran out: its outputs
+                                are incomplete; the device and the handle stay usable           */
+#define ODWF_ESPECTRUM  -8   /* heat-bath: the spectrum of X estimated by Lanczos lies outside
+                                the interval of the rational approximation                      */
 
 /* arithmetic of a call */
 #define ODWF_PREC_DOUBLE 0   /* FP64 storage and arithmetic                                    */
@@ -86,6 +90,11 @@ typedef struct {
     double rat_err;          /* target max relative error of the rational approximation (1e-11)   */
     int    n_poles_out;      /* written: number of poles used                                      */
     int    iters_out;        /* written: Krylov iterations summed over poles                       */
+    int    check_iters;      /* > 0: first estimate the extreme eigenvalues of X with this many
+                                Lanczos steps from eta (eofa_term_spectrum) and return
+                                ODWF_ESPECTRUM if they fall outside [x_lo, x_hi]                   */
+    double ritz_lo_out;      /* written when check_iters > 0: smallest / largest Ritz value        */
+    double ritz_hi_out;
 } odwf_hb_opts;
 
 /* Create a handle for an Lx x Ly x Lz x Lt lattice (all even, each >= 2) with Ns slices
@@ -104,8 +113,11 @@ int odwf_set_gauge(odwf_t* h, const void* U, void* stream);
 
 /* out = Op(m1, m2) in, or its adjoint, on full 5D fields (device, complex128, ABI layout): D_T of
  * Eq.(DTm1m2), H_T = gamma_5 R5 D_T (after Eq.(m1m2_m3m2)) or D_odwf (Eq.(detDodwf)), see ODWF_OP_*.
- * prec: ODWF_PREC_DOUBLE or ODWF_PREC_SINGLE (arithmetic of the hopping and fifth-dimension
- * kernels; in/out stay FP64). in and out must not overlap. */
+ * prec: storage and arithmetic of the hopping and fifth-dimension kernels, in/out staying FP64:
+ * ODWF_PREC_DOUBLE, ODWF_PREC_SINGLE, or ODWF_PREC_HALF (the input and every intermediate stored as
+ * FP16 with one FP32 scale per (site, s), FP32 arithmetic: relative error a few 1e-4). in and out
+ * must not overlap. Returns ODWF_EFAULT (after synchronising `stream`) if a bulk-staged kernel's
+ * bounded wait ran out during the call. */
 int odwf_apply(odwf_t* h, int op, double m1, double m2, const void* in, void* out, int prec, void* stream);
 int odwf_apply_dag(odwf_t* h, int op, double m1, double m2, const void* in, void* out, int prec, void* stream);
 
@@ -116,7 +128,8 @@ int odwf_apply_dag(odwf_t* h, int op, double m1, double m2, const void* in, void
  * work fields and allocates nothing; lattices whose four even-odd half fields plus coefficients
  * exceed 32 MiB (Vh * Ns above ~43,000 in FP64, ~87,000 in FP32) are rejected with ODWF_EINVAL.
  * The first call on each device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current, so make that first call before any stream capture. Every call shares the
+ * that device current. Each call copies its fifth-dimension coefficients from pageable host memory,
+ * so do not call it while `stream` is being captured into a CUDA graph. Every call shares the
  * array: calls whose GPU work overlaps race on it. The handle itself is created by odwf_create. */
 int odwf_apply_noalloc(odwf_t* h, int op, double m1, double m2, const void* in, void* out, int prec, void* stream);
 
@@ -161,6 +174,16 @@ int eofa_force(odwf_t* h, const eofa_term* term, const void* phi, double* F,
  * all poles solved as one batch. eta, phi: 4D device fields; phi gets only the term's chirality. */
 int eofa_heatbath(odwf_t* h, const eofa_term* term, const void* eta, void* phi,
                   odwf_hb_opts* opts, void* stream);
+
+/* Extreme eigenvalues of a term's 4D operator X (the operator of eofa_action) estimated by n_iter
+ * (1..1000) steps of the Lanczos recurrence in FP64, started from P v0 (v0: 4D device field, only the
+ * term's chirality is used; it must not vanish there). Each step applies X once, i.e. one H_T(m3, m4)
+ * solve with `opts` (NULL: FP64 defaults). Writes the smallest and largest Ritz values, which lie
+ * inside the spectrum of X and approach its ends as n_iter grows. The paper states X > 0 (Section 1)
+ * and leaves the heat-bath's spectral interval to the implementer (Eq.(CG_gaussian)); this call lets
+ * a caller check or choose that interval. Synchronises `stream`. */
+int eofa_term_spectrum(odwf_t* h, const eofa_term* term, const void* v0, int n_iter, double* lo, double* hi,
+                       const odwf_solve_opts* opts, void* stream);
 
 /* ---- learned preconditioner (not in the paper) ----------------------------------------------
  * A gauge-equivariant two-layer network of parallel-transport convolutions approximating S^{-1}

@@ -20,7 +20,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import fifth
+from . import fifth, su3
 from .operators import ODWF
 from .rational import InvSqrtRational, inv_sqrt_for_error
 from .solver import solve_ht
@@ -147,8 +147,7 @@ def action(op: ODWF, term: Term, phi, tol=1e-12):
 
 
 def _t_generators():
-    from paper_1710_09621_gb300.inputs import gell_mann
-    return 0.5 * gell_mann()
+    return su3.generators()
 
 
 def dS_dw_from_chi(op: ODWF, term: Term, chi):

@@ -19,6 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libodwf.so")
 
 ODWF_OK, ODWF_EINVAL, ODWF_ENOMEM, ODWF_ECUDA, ODWF_ENOCONV, ODWF_EBREAKDOWN, ODWF_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+ODWF_EFAULT, ODWF_ESPECTRUM = -7, -8
 PREC_DOUBLE, PREC_SINGLE, PREC_HALF = 0, 1, 2
 OP_DT, OP_HT, OP_DODWF = 0, 1, 2
 _PREC = {"double": PREC_DOUBLE, "single": PREC_SINGLE, "half": PREC_HALF,
@@ -31,7 +32,7 @@ EXPORTS = ["odwf_create", "odwf_destroy", "odwf_last_error", "odwf_set_gauge", "
            "odwf_omega_vector", "odwf_profile_enable", "odwf_profile_read", "eofa_mp_terms",
            "odwf_apply_noalloc", "eofa_solve_multi", "odwf_net_create", "odwf_net_destroy",
            "odwf_net_num_params", "odwf_net_weights", "odwf_net_apply", "odwf_net_set_pairs", "odwf_net_loss_grad",
-           "odwf_net_train", "eofa_solve_learned", "odwf_autotune", "eofa_solve_gcr"]
+           "odwf_net_train", "eofa_solve_learned", "odwf_autotune", "eofa_solve_gcr", "eofa_term_spectrum"]
 
 
 class OdwfError(RuntimeError):
@@ -61,7 +62,8 @@ class Term(ctypes.Structure):
 
 class HbOpts(ctypes.Structure):
     _fields_ = [("solve", SolveOpts), ("x_lo", ctypes.c_double), ("x_hi", ctypes.c_double),
-                ("rat_err", ctypes.c_double), ("n_poles_out", ctypes.c_int), ("iters_out", ctypes.c_int)]
+                ("rat_err", ctypes.c_double), ("n_poles_out", ctypes.c_int), ("iters_out", ctypes.c_int),
+                ("check_iters", ctypes.c_int), ("ritz_lo_out", ctypes.c_double), ("ritz_hi_out", ctypes.c_double)]
 
 
 _lib = None
@@ -91,6 +93,7 @@ def load_library(path: str = LIB_PATH):
     lib.eofa_force.argtypes = [vp, ctypes.POINTER(Term), vp, vp, ctypes.POINTER(SolveOpts),
                                ctypes.POINTER(SolveStats), vp]
     lib.eofa_heatbath.argtypes = [vp, ctypes.POINTER(Term), vp, vp, ctypes.POINTER(HbOpts), vp]
+    lib.eofa_term_spectrum.argtypes = [vp, ctypes.POINTER(Term), vp, i, dp, dp, ctypes.POINTER(SolveOpts), vp]
     lib.eofa_k.argtypes = [d, d]
     lib.eofa_k.restype = d
     lib.odwf_omega_vector.argtypes = [vp, i, dp]
@@ -202,7 +205,8 @@ class ODWF:
         return out
 
     def solve(self, b, m1, m2, x=None, opts=None, stream=None, allow_noconv=False):
-        """x = H_T(m1, m2)^{-1} b; returns (x, stats dict)."""
+        """x = H_T(m1, m2)^{-1} b; returns (x, stats dict). With allow_noconv a solve that stops above
+        tol (maxiter or max_seconds) returns its last iterate with "status" instead of raising."""
         import torch
         self._field(b, self.shape5)
         x = torch.empty_like(b) if x is None else self._field(x, self.shape5)
@@ -210,7 +214,7 @@ class ODWF:
         o = opts if opts is not None else solve_opts()
         rc = self.lib.eofa_solve(self.h, float(m1), float(m2), _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(st),
                                  _stream_ptr(stream))
-        self._check(rc, allow=(ODWF_ENOCONV,) if allow_noconv else ())
+        self._check(rc, allow=(ODWF_ENOCONV, ODWF_ETIMEOUT) if allow_noconv else ())
         d = st.as_dict()
         d["status"] = rc
         return x, d
@@ -269,15 +273,31 @@ class ODWF:
                                         ctypes.byref(st), _stream_ptr(stream)))
         return F, st.as_dict()
 
-    def heatbath(self, term: TermSpec, eta, opts=None, x_lo=0.0, x_hi=1.0, rat_err=1e-11, stream=None):
+    def heatbath(self, term: TermSpec, eta, opts=None, x_lo=0.0, x_hi=1.0, rat_err=1e-11, check_iters=0,
+                 stream=None):
+        """phi = X^{-1/2} eta; with check_iters > 0 the spectrum of X is first estimated by Lanczos and
+        an interval [x_lo, x_hi] that does not contain the Ritz values raises ODWF_ESPECTRUM."""
         import torch
         self._field(eta, self.shape4)
         phi = torch.empty_like(eta)
-        hb = HbOpts(opts if opts is not None else solve_opts(), x_lo, x_hi, rat_err, 0, 0)
+        hb = HbOpts(opts if opts is not None else solve_opts(), x_lo, x_hi, rat_err, 0, 0, int(check_iters), 0.0, 0.0)
         t = term.c()
         self._check(self.lib.eofa_heatbath(self.h, ctypes.byref(t), _ptr(eta), _ptr(phi), ctypes.byref(hb),
                                            _stream_ptr(stream)))
-        return phi, {"n_poles": hb.n_poles_out, "iters": hb.iters_out}
+        info = {"n_poles": hb.n_poles_out, "iters": hb.iters_out}
+        if check_iters > 0:
+            info["ritz"] = (hb.ritz_lo_out, hb.ritz_hi_out)
+        return phi, info
+
+    def term_spectrum(self, term: TermSpec, v0, n_iter=12, opts=None, stream=None):
+        """(smallest, largest) Ritz value of the term's operator X after n_iter Lanczos steps from P v0."""
+        self._field(v0, self.shape4)
+        lo, hi = ctypes.c_double(), ctypes.c_double()
+        o = opts if opts is not None else solve_opts()
+        t = term.c()
+        self._check(self.lib.eofa_term_spectrum(self.h, ctypes.byref(t), _ptr(v0), int(n_iter), ctypes.byref(lo),
+                                                ctypes.byref(hi), ctypes.byref(o), _stream_ptr(stream)))
+        return lo.value, hi.value
 
     def autotune(self, prec="single", stream=None):
         """Pick the fastest launch choice of each fused CGNE kernel; returns the timing report."""

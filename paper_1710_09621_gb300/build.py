@@ -7,7 +7,9 @@ source tree, not from site-packages.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import hashlib
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -47,12 +49,31 @@ def _compile(src: str) -> str:
     return obj
 
 
+STAMP = LIB + ".stamp"
+
+
+def source_hash() -> str:
+    """SHA-256 over every source and header, the compile flags, the source list and the host
+    architecture: the library is rebuilt whenever any of them differs from the one it was built from
+    (file times are not used, so a library copied in from elsewhere is never mistaken for current)."""
+    hs = hashlib.sha256()
+    hs.update(platform.machine().encode())
+    hs.update(" ".join(_flags() + SOURCES).replace(ROOT, "<root>").encode())
+    for d in (CSRC, INCLUDE):
+        for f in sorted(os.listdir(d)):
+            fp = os.path.join(d, f)
+            if os.path.isfile(fp):
+                hs.update(f.encode())
+                with open(fp, "rb") as fh:
+                    hs.update(fh.read())
+    return hs.hexdigest()
+
+
 def _stale() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
         return True
-    t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
-    return any(os.path.getmtime(d) > t for d in deps)
+    with open(STAMP) as fh:
+        return fh.read().strip() != source_hash()
 
 
 def build(force: bool = False) -> str:
@@ -68,6 +89,8 @@ def build(force: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as fh:
+        fh.write(source_hash() + "\n")
     return LIB
 
 

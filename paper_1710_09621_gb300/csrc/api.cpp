@@ -37,6 +37,20 @@ int cuda_check(odwf_s* h, cudaError_t e, const char* what) {
     return set_err(h, ODWF_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+int check_fault(odwf_s* h, cudaStream_t st) {
+    if (!h->staged_used) return ODWF_OK;
+    int rc = cuda_check(h, cudaMemcpyAsync(h->fault_host, h->fault, sizeof(unsigned int), cudaMemcpyDeviceToHost, st),
+                        "fault word D2H");
+    if (!rc) rc = cuda_check(h, cudaStreamSynchronize(st), "stream sync");
+    if (rc) return rc;
+    h->staged_used = false;
+    if (*h->fault_host == 0u) return ODWF_OK;
+    *h->fault_host = 0u;
+    if ((rc = cuda_check(h, cudaMemsetAsync(h->fault, 0, sizeof(unsigned int), st), "fault word reset"))) return rc;
+    return set_err(h, ODWF_EFAULT, "a bulk-staged hop kernel's wait for its neighbour copies ran out; its outputs "
+                                   "are incomplete");
+}
+
 // ---- small dense FP64 linear algebra on the host (Ns <= 32) ------------------------------------
 using Mat = std::vector<double>;  // row-major Ns x Ns
 
@@ -315,6 +329,9 @@ int odwf_create(odwf_t** out, const int dims[4], int Ns, double m0, const double
     if (!rc) rc = alloc(h, (void**)&h->fault, sizeof(unsigned int));
     if (!rc) rc = cuda_check(h, cudaMemset(h->fault, 0, sizeof(unsigned int)), "memset fault");
     if (const char* e = std::getenv("ODWF_STAGED")) h->staged = (e[0] == '1') ? 1 : 0;
+    if (const char* e = std::getenv("ODWF_TEST_WAIT_CYCLES")) h->wait_cycles = std::atoll(e);
+    if (!rc) rc = cuda_check(h, cudaMallocHost((void**)&h->fault_host, sizeof(unsigned int)), "cudaMallocHost fault");
+    if (!rc) *h->fault_host = 0u;
     if (!rc) rc = cuda_check(h, cudaMemset(h->state, 0, sizeof(CGState)), "memset state");
     if (!rc) rc = cuda_check(h, cudaMallocHost((void**)&h->state_host, sizeof(CGState)), "cudaMallocHost state");
     if (rc) {
@@ -344,9 +361,11 @@ int odwf_destroy(odwf_t* h) {
     cudaFree(h->state);
     cudaFree(h->fault);
     if (h->state_host) cudaFreeHost(h->state_host);
+    if (h->fault_host) cudaFreeHost(h->fault_host);
     Workspace& w = h->ws;
     void* ps[] = {w.b_e, w.b_o, w.x_e, w.x_o, w.r64, w.t64, w.bh, w.xi, w.ri, w.pi, w.ti,
-                  w.xi_s, w.ri_s, w.pi_s, w.ti_s, h->f64[0], h->f64[1], h->f64[2], h->f64[3], h->acc4};
+                  w.xi_s, w.ri_s, w.pi_s, w.ti_s, h->f64[0], h->f64[1], h->f64[2], h->f64[3], h->acc4,
+                  h->lz[0], h->lz[1], h->lz[2]};
     for (void* p : ps) cudaFree(p);
     for (Workspace& b : h->bws) {
         void* qs[] = {b.b_e, b.b_o, b.x_e, b.x_o, b.r64, b.t64, b.bh, b.xi, b.ri, b.pi, b.ti, b.xi_s, b.ri_s, b.pi_s, b.ti_s};
@@ -392,11 +411,15 @@ static int check_mass(odwf_s* h, double m) {
 // out_p = A_p-block(own) - 1/2 H in_{1-p}, i.e. D_T (dagger: with transposed s-matrices and
 // gamma_5 on both sides) for one output parity; storage of the fields: `stg`.
 int apply_dt_parity(odwf_s* h, int stg, const SCoef* c, bool dag, int parity, const void* in_other,
-                    const void* own, void* out, cudaStream_t st) {
+                    const void* own, void* out, cudaStream_t st, const float* in_scale, const float* own_scale,
+                    float* out_scale) {
     HopArgs a{};
     a.in = in_other;
     a.own = own;
     a.out = out;
+    a.in_scale = in_scale;
+    a.own_scale = own_scale;
+    a.out_scale = out_scale;
     a.mown = c->dev + (size_t)(dag ? 4 : 0) * h->Ns * h->Ns;
     a.c_hop = -0.5;
     a.g5 = dag ? (G5_HOP_IN | G5_OWN_IN | G5_OUT) : 0;
@@ -408,27 +431,36 @@ static int apply_common(odwf_s* h, int op, double m1, double m2, const void* in,
     if (!h || !in || !out) return set_err(h, ODWF_EINVAL, "null argument");
     if (!h->have_gauge) return set_err(h, ODWF_EINVAL, "odwf_set_gauge has not been called");
     if (op != ODWF_OP_DT && op != ODWF_OP_HT && op != ODWF_OP_DODWF) return set_err(h, ODWF_EINVAL, "bad op");
-    if (prec != ODWF_PREC_DOUBLE && prec != ODWF_PREC_SINGLE) return set_err(h, ODWF_EINVAL, "apply: prec must be DOUBLE or SINGLE");
+    if (prec != ODWF_PREC_DOUBLE && prec != ODWF_PREC_SINGLE && prec != ODWF_PREC_HALF)
+        return set_err(h, ODWF_EINVAL, "apply: prec must be DOUBLE, SINGLE or HALF");
     int rc;
     if ((rc = check_mass(h, m1)) || (rc = check_mass(h, m2))) return rc;
-    const int stg = prec == ODWF_PREC_DOUBLE ? ST_DOUBLE : ST_FLOAT;
-    if ((rc = ensure_workspace(h, ST_DOUBLE))) return rc;
+    const int stg = prec == ODWF_PREC_DOUBLE ? ST_DOUBLE : (prec == ODWF_PREC_SINGLE ? ST_FLOAT : ST_HALF);
+    if ((rc = ensure_workspace(h, stg))) return rc;
     const SCoef* c = get_coef(h, m1, m2);
     if (!c) return ODWF_EINVAL;
     Workspace& w = h->ws;
+    // FP64 / FP32 applies use the FP64-sized fields; FP16 storage uses the inner-solver fields, which
+    // carry the per-(cb, s) scales
     void *ie = w.b_e, *io = w.b_o, *oe = w.x_e, *oo = w.x_o;
+    float *ies = nullptr, *ios = nullptr, *oes = nullptr, *oos = nullptr;
+    if (stg == ST_HALF) {
+        ie = w.pi, io = w.ti, oe = w.xi, oo = w.ri;
+        ies = w.pi_s, ios = w.ti_s, oes = w.xi_s, oos = w.ri_s;
+    }
     if (op == ODWF_OP_DODWF) {
         // D_odwf = W D_T W N (N = omega^{1/2}(1 + L), W = omega^{1/2});  D_odwf^dag = N^T W D_T^dag W
         const double* pre = c->dev + (size_t)(dag ? 10 : 8) * h->Ns * h->Ns;
         const double* post = c->dev + (size_t)(dag ? 12 : 10) * h->Ns * h->Ns;
-        if ((rc = launch_pack5(h, (const double*)in, oe, oo, stg, 0, st))) return rc;
-        if ((rc = launch_smix(h, stg, oe, ie, pre, 1.0, st))) return rc;
-        if ((rc = launch_smix(h, stg, oo, io, pre, 1.0, st))) return rc;
-        if ((rc = apply_dt_parity(h, stg, c, dag, 0, io, ie, oe, st))) return rc;
-        if ((rc = apply_dt_parity(h, stg, c, dag, 1, ie, io, oo, st))) return rc;
-        if ((rc = launch_smix(h, stg, oe, ie, post, 1.0, st))) return rc;
-        if ((rc = launch_smix(h, stg, oo, io, post, 1.0, st))) return rc;
-        return launch_unpack5(h, ie, io, (double*)out, stg, 0, st);
+        if ((rc = launch_pack5(h, (const double*)in, oe, oo, stg, 0, st, oes, oos))) return rc;
+        if ((rc = launch_smix(h, stg, oe, ie, pre, 1.0, st, oes, ies))) return rc;
+        if ((rc = launch_smix(h, stg, oo, io, pre, 1.0, st, oos, ios))) return rc;
+        if ((rc = apply_dt_parity(h, stg, c, dag, 0, io, ie, oe, st, ios, ies, oes))) return rc;
+        if ((rc = apply_dt_parity(h, stg, c, dag, 1, ie, io, oo, st, ies, ios, oos))) return rc;
+        if ((rc = launch_smix(h, stg, oe, ie, post, 1.0, st, oes, ies))) return rc;
+        if ((rc = launch_smix(h, stg, oo, io, post, 1.0, st, oos, ios))) return rc;
+        if ((rc = launch_unpack5(h, ie, io, (double*)out, stg, 0, st, ies, ios))) return rc;
+        return check_fault(h, st);
     }
     // H_T = g5 R5 D_T ; H_T^dag = H_T. D_T^dag = g5 (D_T with transposed M) g5.
     // For H_T: out = g5 R5 D_T in  -> pack in plainly, unpack with R5 g5.
@@ -436,10 +468,11 @@ static int apply_common(odwf_s* h, int op, double m1, double m2, const void* in,
     const bool ht = (op == ODWF_OP_HT);
     const int pack_flag = (ht && dag) ? 1 : 0;
     const int unpack_flag = (ht && !dag) ? 1 : 0;
-    if ((rc = launch_pack5(h, (const double*)in, ie, io, stg, pack_flag, st))) return rc;
-    if ((rc = apply_dt_parity(h, stg, c, dag, 0, io, ie, oe, st))) return rc;
-    if ((rc = apply_dt_parity(h, stg, c, dag, 1, ie, io, oo, st))) return rc;
-    return launch_unpack5(h, oe, oo, (double*)out, stg, unpack_flag, st);
+    if ((rc = launch_pack5(h, (const double*)in, ie, io, stg, pack_flag, st, ies, ios))) return rc;
+    if ((rc = apply_dt_parity(h, stg, c, dag, 0, io, ie, oe, st, ios, ies, oes))) return rc;
+    if ((rc = apply_dt_parity(h, stg, c, dag, 1, ie, io, oo, st, ies, ios, oos))) return rc;
+    if ((rc = launch_unpack5(h, oe, oo, (double*)out, stg, unpack_flag, st, oes, oos))) return rc;
+    return check_fault(h, st);
 }
 
 }  // namespace odwf

@@ -6,8 +6,10 @@
 // with k(m_j, m_i) = 2 (m_j - m_i) / ((1 + m_j)(1 + m_i)) (Eq.(k_ij) at c = 1, lambda = 0) and
 // (Omega_-)_s = (-1)^s omega_s^{-1/2}, (Omega_+)_s = (-1)^(Ns-1-s) omega_s^{-1/2} (Eq.(delta_ij)).
 // Every call needs chi = H_T(m3, m4)^{-1} Omega P phi, i.e. D_T chi = R5 g5 Omega P phi.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -272,6 +274,35 @@ __global__ void k_scale4(const double2* in, double2* out, int V, int chir, doubl
     }
 }
 
+// ---- 4D FP64 vector algebra of the Lanczos estimate (n doubles) -----------------------------------
+// out = ca A + cb B + cc C (any of B, C may be null)
+__global__ void k_lincomb4(double* out, double ca, const double* A, double cb, const double* B, double cc,
+                           const double* C, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        double v = ca * A[i];
+        if (B) v = fma(cb, B[i], v);
+        if (C) v = fma(cc, C[i], v);
+        out[i] = v;
+    }
+}
+
+// per-block partial sums of sum_i A[i] B[i] (the real part of <A, B> for interleaved complex data)
+__global__ void k_dot4(const double* A, const double* B, size_t n, double* partials) {
+    __shared__ double wsum[32];
+    double v = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        v = fma(A[i], B[i], v);
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) wsum[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) b += wsum[q];
+        partials[blockIdx.x] = b;
+    }
+}
+
 // ---- host helpers ------------------------------------------------------------------------------
 static int grid_for(odwf_s* h, size_t n, int block) {
     size_t g = (n + block - 1) / block;
@@ -414,6 +445,122 @@ static int ensure_acc4(odwf_s* h) {
     return ODWF_OK;
 }
 
+// X v = P v -/+ k P Omega^T H_T(m3, m4)^{-1} Omega P v (chirality -1 / +1) for a 4D FP64 field
+static int term_apply(odwf_s* h, const eofa_term* t, const double* v, double* out, const odwf_solve_opts* opts,
+                      int* iters, cudaStream_t st) {
+    odwf_solve_stats ss{};
+    int rc = term_solve(h, t, t->m3, t->m4, v, opts, &ss, st);
+    if (rc != ODWF_OK) return rc;
+    *iters += ss.iters;
+    k_scale4<<<grid_for(h, (size_t)h->V * 12, 256), 256, 0, st>>>((const double2*)v, (double2*)out, h->V,
+                                                                    t->chirality, 1.0);
+    if ((rc = cuda_check(h, cudaGetLastError(), "k_scale4"))) return rc;
+    double om[kMaxNs], w[kMaxNs];
+    omega_vec(h, t->chirality, om);
+    const double sgn = t->chirality < 0 ? -1.0 : 1.0;
+    for (int q = 0; q < h->Ns; ++q) w[q] = sgn * term_k(t) * om[q];
+    return contract(h, t->chirality, w, nullptr, out, 0, st);
+}
+
+// Re <A, B> of two 4D FP64 fields (n doubles), summed on the host in block order (deterministic)
+static int dot4(odwf_s* h, const double* A, const double* B, size_t n, double* out, cudaStream_t st) {
+    int g = grid_for(h, n, 256);
+    if (g > h->partials_n) g = h->partials_n;
+    k_dot4<<<g, 256, 0, st>>>(A, B, n, h->partials);
+    int rc = cuda_check(h, cudaGetLastError(), "k_dot4");
+    if (rc) return rc;
+    std::vector<double> part(g);
+    if ((rc = cuda_check(h, cudaMemcpyAsync(part.data(), h->partials, sizeof(double) * g, cudaMemcpyDeviceToHost, st),
+                         "dot D2H")))
+        return rc;
+    if ((rc = cuda_check(h, cudaStreamSynchronize(st), "sync"))) return rc;
+    double sum = 0.0;
+    for (double p : part) sum += p;
+    *out = sum;
+    return ODWF_OK;
+}
+
+static int lincomb4(odwf_s* h, double* out, double ca, const double* A, double cb, const double* B, double cc,
+                    const double* C, size_t n, cudaStream_t st) {
+    k_lincomb4<<<grid_for(h, n, 256), 256, 0, st>>>(out, ca, A, cb, B, cc, C, n);
+    return cuda_check(h, cudaGetLastError(), "k_lincomb4");
+}
+
+// Smallest or largest eigenvalue of the symmetric tridiagonal matrix (diagonal a[0..n-1], off-diagonal
+// b[1..n-1]) by bisection on the Sturm sequence count (the number of eigenvalues below x).
+static double tridiag_extreme(const std::vector<double>& a, const std::vector<double>& b, bool largest) {
+    const int n = (int)a.size();
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < n; ++i) {  // Gershgorin interval
+        const double r = (i > 0 ? std::fabs(b[i]) : 0.0) + (i + 1 < n ? std::fabs(b[i + 1]) : 0.0);
+        lo = std::min(lo, a[i] - r);
+        hi = std::max(hi, a[i] + r);
+    }
+    auto count_below = [&](double x) {
+        int c = 0;
+        double d = 1.0;
+        for (int i = 0; i < n; ++i) {
+            d = a[i] - x - (i > 0 ? b[i] * b[i] / d : 0.0);
+            if (d == 0.0) d = -1e-300;
+            if (d < 0.0) ++c;
+        }
+        return c;
+    };
+    const int target = largest ? n - 1 : 0;  // find x with count_below(x) == target .. target + 1
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(1.0, std::fabs(hi)); ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (count_below(mid) > target) hi = mid;
+        else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// n_iter steps of Lanczos on X from P v0 (FP64, the last two directions re-orthogonalised once more
+// each step); writes the extreme Ritz values.
+static int term_spectrum(odwf_s* h, const eofa_term* t, const void* v0, int n_iter, double* lo, double* hi,
+                         const odwf_solve_opts* opts, int* iters, cudaStream_t st) {
+    const size_t n = (size_t)h->V * 24;
+    int rc = ensure_acc4(h);
+    if (rc) return rc;
+    for (int i = 0; i < 3 && !rc; ++i)
+        if (!h->lz[i] && cudaMalloc((void**)&h->lz[i], sizeof(double) * n) != cudaSuccess)
+            rc = set_err(h, ODWF_ENOMEM, "cudaMalloc Lanczos vectors");
+    if (rc) return rc;
+    double *vp = h->lz[0], *v = h->lz[1], *w = h->lz[2];
+    k_scale4<<<grid_for(h, (size_t)h->V * 12, 256), 256, 0, st>>>((const double2*)v0, (double2*)v, h->V,
+                                                                    t->chirality, 1.0);
+    if ((rc = cuda_check(h, cudaGetLastError(), "k_scale4"))) return rc;
+    double nrm2 = 0.0;
+    if ((rc = dot4(h, v, v, n, &nrm2, st))) return rc;
+    if (!(nrm2 > 0.0) || !std::isfinite(nrm2)) return set_err(h, ODWF_EINVAL, "Lanczos start vector is zero on the term's chirality");
+    if ((rc = lincomb4(h, v, 1.0 / std::sqrt(nrm2), v, 0.0, nullptr, 0.0, nullptr, n, st))) return rc;
+    if ((rc = cuda_check(h, cudaMemsetAsync(vp, 0, sizeof(double) * n, st), "memset"))) return rc;
+    std::vector<double> al, be(1, 0.0);
+    for (int j = 0; j < n_iter; ++j) {
+        if ((rc = term_apply(h, t, v, w, opts, iters, st))) return rc;
+        double a = 0.0;
+        if ((rc = dot4(h, v, w, n, &a, st))) return rc;
+        // w -= a v + b_j v_prev, then once more against v and v_prev (local re-orthogonalisation)
+        if ((rc = lincomb4(h, w, 1.0, w, -a, v, -be[j], vp, n, st))) return rc;
+        double c1 = 0.0, c2 = 0.0;
+        if ((rc = dot4(h, v, w, n, &c1, st)) || (rc = dot4(h, vp, w, n, &c2, st))) return rc;
+        if ((rc = lincomb4(h, w, 1.0, w, -c1, v, -c2, vp, n, st))) return rc;
+        al.push_back(a + c1);
+        double b2 = 0.0;
+        if ((rc = dot4(h, w, w, n, &b2, st))) return rc;
+        const double b = std::sqrt(std::max(b2, 0.0));
+        if (j + 1 == n_iter || !(b > 1e-12 * std::fabs(a))) break;  // invariant subspace found
+        be.push_back(b);
+        // v_prev <- v, v <- w / b
+        std::swap(vp, v);
+        if ((rc = lincomb4(h, v, 1.0 / b, w, 0.0, nullptr, 0.0, nullptr, n, st))) return rc;
+    }
+    be.resize(al.size());
+    *lo = tridiag_extreme(al, be, false);
+    *hi = tridiag_extreme(al, be, true);
+    return ODWF_OK;
+}
+
 }  // namespace odwf
 
 using namespace odwf;
@@ -458,6 +605,17 @@ extern "C" int eofa_force(odwf_t* h, const eofa_term* t, const void* phi, double
     return src;
 }
 
+extern "C" int eofa_term_spectrum(odwf_t* h, const eofa_term* t, const void* v0, int n_iter, double* lo, double* hi,
+                                  const odwf_solve_opts* opts, void* stream) {
+    if (!h || !v0 || !lo || !hi) return set_err(h, ODWF_EINVAL, "null argument");
+    if (!h->have_gauge) return set_err(h, ODWF_EINVAL, "odwf_set_gauge has not been called");
+    if (n_iter < 1 || n_iter > 1000) return set_err(h, ODWF_EINVAL, "n_iter must lie in 1..1000");
+    int rc = check_term(h, t);
+    if (rc) return rc;
+    int iters = 0;
+    return term_spectrum(h, t, v0, n_iter, lo, hi, opts, &iters, (cudaStream_t)stream);
+}
+
 extern "C" int eofa_heatbath(odwf_t* h, const eofa_term* t, const void* eta, void* phi, odwf_hb_opts* hb,
                              void* stream) {
     if (!h || !eta || !phi) return set_err(h, ODWF_EINVAL, "null argument");
@@ -477,6 +635,23 @@ extern "C" int eofa_heatbath(odwf_t* h, const eofa_term* t, const void* eta, voi
         if (hb->rat_err > 0.0) target = hb->rat_err;
     }
     if (!(x_lo > 0.0 && x_hi > x_lo)) return set_err(h, ODWF_EINVAL, "bad spectral interval");
+    if (hb && hb->check_iters > 0) {
+        // Lanczos on X from eta: its extreme Ritz values lie inside the spectrum of X and approach its
+        // ends; an interval that does not contain them cannot contain the spectrum
+        double rlo = 0.0, rhi = 0.0;
+        int it = 0;
+        odwf_solve_opts co = so;
+        if (co.tol < 1e-8) co.tol = 1e-8;
+        if ((rc = term_spectrum(h, t, eta, hb->check_iters, &rlo, &rhi, &co, &it, st))) return rc;
+        hb->ritz_lo_out = rlo;
+        hb->ritz_hi_out = rhi;
+        if (rlo < x_lo || rhi > x_hi) {
+            char buf[200];
+            std::snprintf(buf, sizeof buf, "spectrum of X estimated as [%.6g, %.6g] by Lanczos, outside the interval "
+                          "[%.6g, %.6g] of the rational approximation", rlo, rhi, x_lo, x_hi);
+            return set_err(h, ODWF_ESPECTRUM, buf);
+        }
+    }
     Rational r;
     int n = 1;
     for (; n <= 64; ++n) {

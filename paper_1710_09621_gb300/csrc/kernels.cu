@@ -450,9 +450,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Wait for phase `parity` for at most ~1 s of SM clock; false on time-out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` for at most ~1 s of SM clock (limit <= 0), or for at most `limit` cycles
+// polled with the non-blocking test (a caller-set limit, which tests use to make the wait run out);
+// false on time-out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit = 0) {
     const long long t0 = clock64();
+    if (limit > 0) {
+        while (!mbar_test_wait(bar, parity))
+            if (clock64() - t0 > limit) return false;
+        return true;
+    }
     while (!mbar_try_wait(bar, parity)) {
         if (clock64() - t0 > 2000000000LL) return false;
     }
@@ -638,15 +655,19 @@ __device__ __forceinline__ void hop_body_staged(const HopArgs& a) {
             }
         }
         if (tid == 0) {
-            bool ok = mbar_wait_bounded(bar, phase);
+            bool ok = mbar_wait_bounded(bar, phase, a.wait_cycles);
             if (!ok) {
                 if (a.fault) atomicOr(a.fault, 1u);
-                mbar_wait_bounded(bar, phase);  // give copies still in flight a last chance to land
+                // the copies of this phase still target this CTA's shared memory: wait for them with
+                // the full limit before the CTA leaves its groups
+                mbar_wait_bounded(bar, phase);
             }
             ok_s = ok;
         }
         __syncthreads();
-        if (!ok_s) return;
+        // on a time-out the CTA skips its remaining groups but still joins the grid reduction, so
+        // the reduction ticket of the solver state stays consistent
+        if (!ok_s) break;
         phase ^= 1u;
         float v[24];
 #pragma unroll
@@ -766,6 +787,7 @@ void hop_fill(odwf_s* h, int storage, int parity, HopArgs& a, bool reduces) {
     a.Ns = h->Ns;
     a.parity = parity;
     a.fault = h->fault;
+    a.wait_cycles = h->wait_cycles;
     if (a.partials == nullptr) a.partials = h->partials;
     if (reduces && a.state == nullptr) a.state = h->state;
 }
@@ -859,6 +881,7 @@ static int launch_multi_one(odwf_s* h, const HopArgs* dev_args, int n, int max_v
     if (gx < 1) gx = 1;
     if constexpr (KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::CAN_STAGE) {
         if (stg) {
+            h->staged_used = true;
             k_hop_staged_multi<ST, MIXHOP, OWN, MIXOWN, EPI><<<dim3(gx, n), dim3(h->Ns, spb), smem, st>>>(dev_args);
             return cuda_check(h, cudaGetLastError(), "k_hop_staged_multi launch");
         }
@@ -892,6 +915,7 @@ static int launch_one(odwf_s* h, int parity, HopArgs a, cudaStream_t st) {
     bool plain = true;
     if constexpr (KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::CAN_STAGE) {
         if (stg) {
+            h->staged_used = true;
             k_hop_staged<ST, MIXHOP, OWN, MIXOWN, EPI><<<grid, dim3(Ns, spb), smem, st>>>(a);
             plain = false;
         }
@@ -965,14 +989,18 @@ int launch_hop_own_cgb(odwf_s* h, int storage, HopArgs a, cudaStream_t st) {
     return set_err(h, ODWF_EINVAL, "bad storage");
 }
 
-int launch_smix(odwf_s* h, int storage, const void* in, void* out, const double* mt, double, cudaStream_t st) {
+int launch_smix(odwf_s* h, int storage, const void* in, void* out, const double* mt, double, cudaStream_t st,
+                const float* in_scale, float* out_scale) {
     HopArgs a{};
     a.own = in;
     a.out = out;
     a.mown = mt;
+    a.own_scale = in_scale;
+    a.out_scale = out_scale;
     switch (storage) {
         case ST_DOUBLE: return launch_st<ST_DOUBLE>(h, 0, false, false, true, true, EPI_STORE, a, st);
         case ST_FLOAT: return launch_st<ST_FLOAT>(h, 0, false, false, true, true, EPI_STORE, a, st);
+        case ST_HALF: return launch_st<ST_HALF>(h, 0, false, false, true, true, EPI_STORE, a, st);
     }
     return set_err(h, ODWF_EINVAL, "bad storage for smix");
 }
@@ -1051,7 +1079,8 @@ struct ProfScope {
     }
 };
 
-int launch_pack5(odwf_s* h, const double* lex5, void* e, void* o, int storage, int r5g5, cudaStream_t st) {
+int launch_pack5(odwf_s* h, const double* lex5, void* e, void* o, int storage, int r5g5, cudaStream_t st,
+                 float* es, float* os) {
     ProfScope ps(h, 1, ST_DOUBLE, storage, st);
     const size_t n = (size_t)2 * h->Vh * h->Ns;
     const int g = grid_1d(h, n);
@@ -1061,12 +1090,16 @@ int launch_pack5(odwf_s* h, const double* lex5, void* e, void* o, int storage, i
     else if (storage == ST_FLOAT)
         k_pack5<ST_FLOAT><<<g, 256, 0, st>>>((const double2*)lex5, e, o, nullptr, nullptr, h->lexof[0], h->lexof[1],
                                              h->Vh, h->V, h->Ns, r5g5);
+    else if (storage == ST_HALF && es && os)
+        k_pack5<ST_HALF><<<g, 256, 0, st>>>((const double2*)lex5, e, o, es, os, h->lexof[0], h->lexof[1], h->Vh,
+                                            h->V, h->Ns, r5g5);
     else
         return set_err(h, ODWF_EINVAL, "pack5: storage");
     return cuda_check(h, cudaGetLastError(), "k_pack5");
 }
 
-int launch_unpack5(odwf_s* h, const void* e, const void* o, double* lex5, int storage, int r5g5, cudaStream_t st) {
+int launch_unpack5(odwf_s* h, const void* e, const void* o, double* lex5, int storage, int r5g5, cudaStream_t st,
+                   const float* es, const float* os) {
     ProfScope ps(h, 2, storage, ST_DOUBLE, st);
     const size_t n = (size_t)2 * h->Vh * h->Ns;
     const int g = grid_1d(h, n);
@@ -1076,6 +1109,9 @@ int launch_unpack5(odwf_s* h, const void* e, const void* o, double* lex5, int st
     else if (storage == ST_FLOAT)
         k_unpack5<ST_FLOAT><<<g, 256, 0, st>>>(e, o, nullptr, nullptr, (double2*)lex5, h->lexof[0], h->lexof[1],
                                                h->Vh, h->V, h->Ns, r5g5);
+    else if (storage == ST_HALF && es && os)
+        k_unpack5<ST_HALF><<<g, 256, 0, st>>>(e, o, es, os, (double2*)lex5, h->lexof[0], h->lexof[1], h->Vh, h->V,
+                                              h->Ns, r5g5);
     else
         return set_err(h, ODWF_EINVAL, "unpack5: storage");
     return cuda_check(h, cudaGetLastError(), "k_unpack5");

@@ -1256,6 +1256,8 @@ extern "C" int eofa_solve_learned(odwf_t* h, odwf_net_t* n, double m1, double m2
     float *z = n->f[3], *wv = n->f[4], *mv = n->f[5], *xi = n->f[6], *rho = n->f[7], *p = n->sf[0], *t = n->sf[1];
     double bnorm2 = 0.0, rr64 = 0.0;
     if ((rc = schur_start(h, c, b, &bnorm2, &rr64, st))) return rc;
+    if (!std::isfinite(bnorm2) || !std::isfinite(rr64))
+        return set_err(h, ODWF_EBREAKDOWN, "non-finite right-hand side (|b|^2 is not finite)");
     const double tol2 = o.tol * o.tol * bnorm2;
     int iters = 0, cycles = 0;
     const double delta = (o.delta > 0 && o.delta < 1) ? o.delta : 1e-3;
@@ -1328,6 +1330,7 @@ extern "C" int eofa_solve_learned(odwf_t* h, odwf_net_t* n, double m1, double m2
     }
     double res = 0.0;
     if ((rc = schur_finish(h, c, x, bnorm2, &res, st))) return rc;
+    if ((rc = check_fault(h, st))) return rc;
     if (stats) {
         stats->iters = iters;
         stats->reliable_updates = cycles;
@@ -1585,6 +1588,8 @@ extern "C" int eofa_solve_gcr(odwf_t* h, odwf_net_t* n, double m1, double m2, co
     const size_t b32 = half32(h), n4 = b32 / sizeof(float4);
     double bnorm2 = 0.0, rr64 = 0.0;
     if ((rc = schur_start(h, c, b, &bnorm2, &rr64, st))) return rc;
+    if (!std::isfinite(bnorm2) || !std::isfinite(rr64))
+        return set_err(h, ODWF_EBREAKDOWN, "non-finite right-hand side (|b|^2 is not finite)");
     const double tol2 = o.tol * o.tol * bnorm2;
     const double delta = (o.delta > 0 && o.delta < 1) ? o.delta : 1e-3;
     int iters = 0, cycles = 0;
@@ -1636,6 +1641,7 @@ extern "C" int eofa_solve_gcr(odwf_t* h, odwf_net_t* n, double m1, double m2, co
     }
     double res = 0.0;
     if ((rc = schur_finish(h, c, x, bnorm2, &res, st))) return rc;
+    if ((rc = check_fault(h, st))) return rc;
     if (stats) {
         stats->iters = iters;
         stats->reliable_updates = cycles;

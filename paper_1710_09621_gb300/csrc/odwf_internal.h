@@ -83,6 +83,7 @@ struct HopArgs {
     int slot;            // result slot of NORM / RESID
     int parity;          // output parity (bulk-staged kernels derive in-block neighbours from it)
     unsigned int* fault; // set to 1 if a bulk-copy wait ran out of time (never expected)
+    long long wait_cycles;  // limit of the bulk-copy wait in SM clock cycles (0: the default, ~1 s)
 };
 
 // ---- host-side handle --------------------------------------------------------------------------
@@ -132,7 +133,11 @@ struct odwf_s {
     void* f64[4] = {nullptr, nullptr, nullptr, nullptr};
     // 4D scratch
     double* acc4 = nullptr;
+    double* lz[3] = {nullptr, nullptr, nullptr};  // Lanczos vectors of eofa_term_spectrum (4D FP64)
     unsigned int* fault = nullptr;        // device word, see HopArgs::fault
+    unsigned int* fault_host = nullptr;   // pinned mirror of the fault word
+    bool staged_used = false;             // a bulk-staged kernel ran since the fault word was last read
+    long long wait_cycles = 0;            // HopArgs::wait_cycles (ODWF_TEST_WAIT_CYCLES, tests only)
     int staged = 0;                       // use the bulk-staged hop kernels where they apply (ODWF_STAGED=1)
     // autotuned launch choice per kernel variant (key without the staged flag): grid mode, staged
     std::map<int, std::pair<int, int>> tune;
@@ -168,23 +173,29 @@ inline size_t half_elems_bytes(const odwf_s* h, int st) {
 }
 
 int set_err(odwf_s* h, int code, const std::string& msg);
+// After work that may have run bulk-staged kernels: synchronise `st`, read and clear the fault word,
+// and return ODWF_EFAULT if a bounded wait ran out (ODWF_OK otherwise, at once if no staged kernel ran).
+int check_fault(odwf_s* h, cudaStream_t st);
 int ensure_ws(odwf_s* h, Workspace& w, int inner);
 int ensure_workspace(odwf_s* h, int inner);
 int cuda_check(odwf_s* h, cudaError_t e, const char* what);
 const SCoef* get_coef(odwf_s* h, double m1, double m2);
 bool coef_host(const odwf_s* h, double m1, double m2, std::vector<double>& host, std::string& err);
+// FP16 storage passes the per-(cb, s) scales of the three fields (ignored for FP64 / FP32)
 int apply_dt_parity(odwf_s* h, int stg, const SCoef* c, bool dag, int parity, const void* in_other,
-                    const void* own, void* out, cudaStream_t st);
+                    const void* own, void* out, cudaStream_t st, const float* in_scale = nullptr,
+                    const float* own_scale = nullptr, float* out_scale = nullptr);
 
 // launch helpers (kernels.cu)
 // Generic hop: out_p = epi( [MIXOWN ? Mown own : 0] + Mhop?( c_hop H in + a_own own ) )
 int launch_hop(odwf_s* h, int storage, int parity, bool mixhop, bool own, bool mixown, int epi,
                HopArgs a, cudaStream_t st);
 int launch_smix(odwf_s* h, int storage, const void* in, void* out, const double* mt, double scale,
-                cudaStream_t st);
-int launch_pack5(odwf_s* h, const double* lex5, void* e, void* o, int storage, int r5g5, cudaStream_t st);
+                cudaStream_t st, const float* in_scale = nullptr, float* out_scale = nullptr);
+int launch_pack5(odwf_s* h, const double* lex5, void* e, void* o, int storage, int r5g5, cudaStream_t st,
+                 float* e_scale = nullptr, float* o_scale = nullptr);
 int launch_unpack5(odwf_s* h, const void* e, const void* o, double* lex5, int storage, int r5g5,
-                   cudaStream_t st);
+                   cudaStream_t st, const float* e_scale = nullptr, const float* o_scale = nullptr);
 int launch_convert(odwf_s* h, const void* in, int st_in, const float* in_scale, void* out, int st_out,
                    float* out_scale, cudaStream_t st);
 int launch_axpy_to64(odwf_s* h, double a, const void* xin, int st_in, const float* xin_scale, double* y,

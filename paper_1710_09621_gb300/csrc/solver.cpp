@@ -295,6 +295,11 @@ int solve_slots(std::vector<Slot>& S, const odwf_solve_opts* opts_in, cudaStream
         s.bnorm2 = s.hstate->result[0] + s.hstate->result[1];
         s.rr64 = s.hstate->result[2];
         s.tol2 = o.tol * o.tol * s.bnorm2;
+        if (!std::isfinite(s.bnorm2) || !std::isfinite(s.rr64)) {
+            s.status = set_err(s.h, ODWF_EBREAKDOWN, "non-finite right-hand side (|b|^2 is not finite)");
+            s.done = true;
+            continue;
+        }
         if (s.bnorm2 == 0.0 || s.rr64 <= s.tol2) {
             s.done = true;
             continue;
@@ -467,6 +472,12 @@ int solve_slots(std::vector<Slot>& S, const odwf_solve_opts* opts_in, cudaStream
     if ((rc = sync(h0, st))) return rc;
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     int worst = ODWF_OK;
+    // a bulk-staged kernel whose bounded wait ran out left part of its outputs unwritten
+    for (Slot& s : S)
+        if ((rc = check_fault(s.h, st))) {
+            if (rc != ODWF_EFAULT) return rc;
+            s.status = rc;
+        }
     for (Slot& s : S) {
         s.stats.iters = s.iters;
         s.stats.reliable_updates = s.updates;
@@ -479,6 +490,7 @@ int solve_slots(std::vector<Slot>& S, const odwf_solve_opts* opts_in, cudaStream
                                                           std::to_string(s.iters) + " iterations");
         }
         if (s.status != ODWF_OK && (worst == ODWF_OK || worst == ODWF_ENOCONV)) worst = s.status;
+        if (s.status == ODWF_EFAULT) worst = ODWF_EFAULT;
     }
     return worst;
 }

@@ -120,6 +120,10 @@ def test_train_and_solve(env):
     _, st3 = lat.solve(torch.from_numpy(b).cuda(), M1, M2, opts=binding.solve_opts(tol=1e-10, prec="single"))
     print(f"\nloss {losses[0]:.4e} -> {losses[-1]:.4e}; iterations: trained {st['iters']}, "
           f"Neumann {st2['iters']}, plain CGNE {st3['iters']}")
+    # the preconditioned solve needs fewer iterations than the method without the network, and training
+    # does not make the network worse than its Neumann starting point
+    assert st["iters"] < st3["iters"] and st2["iters"] < st3["iters"]
+    assert st["iters"] <= 1.05 * st2["iters"]
 
 
 @pytest.mark.parametrize("which,truncate", [("none", False), ("neumann", False), ("trained", False),

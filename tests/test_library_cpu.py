@@ -27,6 +27,9 @@ def test_library_builds_and_exports_every_symbol():
     lib = ctypes.CDLL(path)
     for name in _declared():
         assert hasattr(lib, name), name
+    # the library on disk was built from exactly these sources, flags and host architecture
+    with open(build.STAMP) as fh:
+        assert fh.read().strip() == build.source_hash()
 
 
 def test_binding_fails_loudly_without_library(tmp_path):

@@ -8,7 +8,7 @@ and heat-bath of the oracle are checked against dense linear algebra and finite 
 import numpy as np
 import pytest
 
-from oracle import eofa, fifth, rational, solver
+from oracle import eofa, fifth, rational, solver, su3
 from oracle.operators import ODWF
 from oracle.wilson import GAMMA5, spin_mul
 from paper_1710_09621_gb300.inputs import (gaussian_spinor, gaussian_spinor5, omega_shamir,
@@ -156,7 +156,7 @@ def test_force_finite_difference(term):
     phi = gaussian_spinor(dims, 7)
     op = ODWF(U, 1.3, om)
     F, _ = eofa.force(op, term, phi, tol=1e-14)
-    ta = 0.5 * __import__("paper_1710_09621_gb300.inputs", fromlist=["gell_mann"]).gell_mann()
+    ta = su3.generators()
     rng = np.random.default_rng(1)
     Lx, Ly, Lz, Lt = dims
 
