@@ -185,6 +185,58 @@ int eofa_heatbath(odwf_t* h, const eofa_term* term, const void* eta, void* phi,
 int eofa_term_spectrum(odwf_t* h, const eofa_term* term, const void* v0, int n_iter, double* lo, double* hi,
                        const odwf_solve_opts* opts, void* stream);
 
+/* ---- HMC molecular dynamics (Section 1: HMC outline, Eq.(molecular_U), Eq.(molecular_P);
+ * Section 3: Omelyan integrator, multiple time scales, Wilson plaquette gauge action) -------------
+ * U_l = exp(i A_l^a t^a), t^a = lambda^a / 2; momenta P_l = P_l^a t^a with H = 1/2 sum (P_l^a)^2 + S_g +
+ * sum of the EOFA terms' actions; forces F^a = -dS/dw^a for U -> exp(i w^a t^a) U (as eofa_force).
+ * Fields: U the ABI gauge layout (device, complex128, updated in place where stated), P and F device
+ * double [4][V][8] (mu, lexicographic site, a). All of it is FP64. Every call synchronises `stream`
+ * when it returns a host scalar. */
+
+/* S_g = beta sum_{x, mu < nu} (1 - Re tr U_{mu nu}(x) / 3), U_{mu nu}(x) = U_mu(x) U_nu(x+mu)
+ * U_mu(x+nu)^dag U_nu(x)^dag (periodic links), written to *S. */
+int hmc_gauge_action(odwf_t* h, const void* U, double beta, double* S, void* stream);
+/* F^a_mu(x) = -dS_g/dw^a = -(beta/3) Im tr(t^a U_mu(x) Sigma_mu(x)), Sigma_mu the sum of the six staples. */
+int hmc_gauge_force(odwf_t* h, const void* U, double beta, double* F, void* stream);
+/* P += eps F (a momentum update of Eq.(molecular_P) with a fixed force). */
+int hmc_momentum_update(odwf_t* h, double* P, const double* F, double eps, void* stream);
+/* U <- exp(i tau P^a t^a) U on every link (Eq.(molecular_U) over time tau at fixed P), in place, with the
+ * exact SU(3) exponential (scaling and squaring of the Taylor series); also reloads the library's
+ * reordered copies of U, so the operator, solve and EOFA calls act on the new links at once. */
+int hmc_link_update(odwf_t* h, void* U, const double* P, double tau, void* stream);
+/* K = 1/2 sum (P^a)^2, written to *K. */
+int hmc_kinetic(odwf_t* h, const double* P, double* K, void* stream);
+
+#define ODWF_HMC_MAX_LEVELS 4
+typedef struct {
+    double dH;              /* H(end) - H(start)                                                    */
+    double K0, K1;          /* kinetic energy at the start and the end                               */
+    double Sg0, Sg1;        /* gauge action                                                          */
+    double Sf0, Sf1;        /* sum of the EOFA terms' actions                                        */
+    int    force_evals[ODWF_HMC_MAX_LEVELS]; /* momentum updates (force evaluations) per level        */
+    int    link_updates;
+    long long cg_iters;     /* Krylov iterations of every solve of the trajectory                    */
+    double seconds;
+} hmc_md_stats;
+
+/* One molecular-dynamics trajectory of length tau (step 5 of the HMC outline in Section 1): the
+ * Omelyan integrator with nlevels time scales (Section 3). Level 0 carries the gauge force with
+ * steps[0] steps per trajectory; EOFA term i (pseudofermion phis[i], fixed, e.g. from eofa_heatbath)
+ * carries its force on level term_level[i] (0 <= level < nlevels), and level l has steps[l] steps
+ * (steps[l] a multiple of 2 steps[l + 1]). One Omelyan step of size e on level l is
+ *   P += lambda e F_l ; levels below over e/2 ; P += (1 - 2 lambda) e F_l ; levels below over e/2 ;
+ *   P += lambda e F_l
+ * and below level 0 is the link update over the half step; the smallest time step is tau/(2 steps[0])
+ * ((k0, k1, k2) = (480, 12, 6) gives 960 link updates). Momentum updates of one level that meet at
+ * the same links are applied as one (so level l evaluates its force 2 steps[l] + 1 times).
+ * lambda: Omelyan's parameter (0.1931833275037836 for the minimum-norm scheme). U and P are
+ * updated in place; stats (may be NULL) receives Delta H = H(end) - H(start) and its parts (each term's
+ * action is one H_T solve at each end), the force evaluations per level and the Krylov iterations.
+ * The accept / reject step and the momentum refresh are the caller's (it draws P). */
+int hmc_md(odwf_t* h, void* U, double* P, double beta, int nterms, const eofa_term* terms,
+           const void* const* phis, const int* term_level, int nlevels, const int* steps, double tau,
+           double lambda, const odwf_solve_opts* opts, hmc_md_stats* stats, void* stream);
+
 /* ---- learned preconditioner (not in the paper) ----------------------------------------------
  * A gauge-equivariant two-layer network of parallel-transport convolutions approximating S^{-1}
  * for the even-odd Schur complement S of D_T(m1, m2) (the system eofa_solve iterates on):

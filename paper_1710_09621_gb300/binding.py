@@ -32,7 +32,9 @@ EXPORTS = ["odwf_create", "odwf_destroy", "odwf_last_error", "odwf_set_gauge", "
            "odwf_omega_vector", "odwf_profile_enable", "odwf_profile_read", "eofa_mp_terms",
            "odwf_apply_noalloc", "eofa_solve_multi", "odwf_net_create", "odwf_net_destroy",
            "odwf_net_num_params", "odwf_net_weights", "odwf_net_apply", "odwf_net_set_pairs", "odwf_net_loss_grad",
-           "odwf_net_train", "eofa_solve_learned", "odwf_autotune", "eofa_solve_gcr", "eofa_term_spectrum"]
+           "odwf_net_train", "eofa_solve_learned", "odwf_autotune", "eofa_solve_gcr", "eofa_term_spectrum",
+           "hmc_gauge_action", "hmc_gauge_force", "hmc_momentum_update", "hmc_link_update", "hmc_kinetic",
+           "hmc_md"]
 
 
 class OdwfError(RuntimeError):
@@ -66,6 +68,23 @@ class HbOpts(ctypes.Structure):
                 ("check_iters", ctypes.c_int), ("ritz_lo_out", ctypes.c_double), ("ritz_hi_out", ctypes.c_double)]
 
 
+HMC_MAX_LEVELS = 4
+OMELYAN_LAMBDA = 0.1931833275037836
+
+
+class HmcStats(ctypes.Structure):
+    _fields_ = [("dH", ctypes.c_double), ("K0", ctypes.c_double), ("K1", ctypes.c_double),
+                ("Sg0", ctypes.c_double), ("Sg1", ctypes.c_double), ("Sf0", ctypes.c_double), ("Sf1", ctypes.c_double),
+                ("force_evals", ctypes.c_int * HMC_MAX_LEVELS), ("link_updates", ctypes.c_int),
+                ("cg_iters", ctypes.c_longlong), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k in ("dH", "K0", "K1", "Sg0", "Sg1", "Sf0", "Sf1", "link_updates", "cg_iters",
+                                           "seconds")}
+        d["force_evals"] = list(self.force_evals)
+        return d
+
+
 _lib = None
 
 
@@ -94,6 +113,13 @@ def load_library(path: str = LIB_PATH):
                                ctypes.POINTER(SolveStats), vp]
     lib.eofa_heatbath.argtypes = [vp, ctypes.POINTER(Term), vp, vp, ctypes.POINTER(HbOpts), vp]
     lib.eofa_term_spectrum.argtypes = [vp, ctypes.POINTER(Term), vp, i, dp, dp, ctypes.POINTER(SolveOpts), vp]
+    lib.hmc_gauge_action.argtypes = [vp, vp, d, dp, vp]
+    lib.hmc_gauge_force.argtypes = [vp, vp, d, vp, vp]
+    lib.hmc_momentum_update.argtypes = [vp, vp, vp, d, vp]
+    lib.hmc_link_update.argtypes = [vp, vp, vp, d, vp]
+    lib.hmc_kinetic.argtypes = [vp, vp, dp, vp]
+    lib.hmc_md.argtypes = [vp, vp, vp, d, i, ctypes.POINTER(Term), ctypes.POINTER(vp), ip, i, ip, d, d,
+                           ctypes.POINTER(SolveOpts), ctypes.POINTER(HmcStats), vp]
     lib.eofa_k.argtypes = [d, d]
     lib.eofa_k.restype = d
     lib.odwf_omega_vector.argtypes = [vp, i, dp]
@@ -298,6 +324,56 @@ class ODWF:
         self._check(self.lib.eofa_term_spectrum(self.h, ctypes.byref(t), _ptr(v0), int(n_iter), ctypes.byref(lo),
                                                 ctypes.byref(hi), ctypes.byref(o), _stream_ptr(stream)))
         return lo.value, hi.value
+
+    # ---- HMC molecular dynamics (momenta / forces: float64 tensors of shape_force) --------------
+    def gauge_action(self, U, beta, stream=None):
+        S = ctypes.c_double()
+        self._check(self.lib.hmc_gauge_action(self.h, _ptr(self._field(U, self.shape_links)), float(beta),
+                                              ctypes.byref(S), _stream_ptr(stream)))
+        return S.value
+
+    def gauge_force(self, U, beta, stream=None):
+        import torch
+        F = torch.empty(self.shape_force, dtype=torch.float64, device=U.device)
+        self._check(self.lib.hmc_gauge_force(self.h, _ptr(self._field(U, self.shape_links)), float(beta), _ptr(F),
+                                             _stream_ptr(stream)))
+        return F
+
+    def momentum_update(self, P, F, eps, stream=None):
+        import torch
+        self._field(P, self.shape_force, torch.float64)
+        self._field(F, self.shape_force, torch.float64)
+        self._check(self.lib.hmc_momentum_update(self.h, _ptr(P), _ptr(F), float(eps), _stream_ptr(stream)))
+
+    def link_update(self, U, P, tau, stream=None):
+        """U <- exp(i tau P) U in place (and the library's copies of U follow)."""
+        import torch
+        self._field(U, self.shape_links)
+        self._field(P, self.shape_force, torch.float64)
+        self._check(self.lib.hmc_link_update(self.h, _ptr(U), _ptr(P), float(tau), _stream_ptr(stream)))
+
+    def kinetic(self, P, stream=None):
+        import torch
+        K = ctypes.c_double()
+        self._check(self.lib.hmc_kinetic(self.h, _ptr(self._field(P, self.shape_force, torch.float64)),
+                                         ctypes.byref(K), _stream_ptr(stream)))
+        return K.value
+
+    def md(self, U, P, beta, terms, phis, levels, steps, tau=1.0, lam=OMELYAN_LAMBDA, opts=None, stream=None):
+        """One MD trajectory (nested Omelyan, multiple time scales): U, P updated in place; returns stats."""
+        import torch
+        self._field(U, self.shape_links)
+        self._field(P, self.shape_force, torch.float64)
+        n = len(terms)
+        tarr = (Term * max(1, n))(*[t.c() for t in terms])
+        parr = (ctypes.c_void_p * max(1, n))(*[self._field(p, self.shape4).data_ptr() for p in phis])
+        larr = (ctypes.c_int * max(1, n))(*[int(l) for l in levels])
+        sarr = (ctypes.c_int * len(steps))(*[int(k) for k in steps])
+        st = HmcStats()
+        o = opts if opts is not None else solve_opts()
+        self._check(self.lib.hmc_md(self.h, _ptr(U), _ptr(P), float(beta), n, tarr, parr, larr, len(steps), sarr,
+                                    float(tau), float(lam), ctypes.byref(o), ctypes.byref(st), _stream_ptr(stream)))
+        return st.as_dict()
 
     def autotune(self, prec="single", stream=None):
         """Pick the fastest launch choice of each fused CGNE kernel; returns the timing report."""

@@ -177,6 +177,51 @@ bool coef_host(const odwf_s* h, double m1, double m2, std::vector<double>& host,
     return true;
 }
 
+bool struct_host(const odwf_s* h, double m1, double m2, SStruct* out) {
+    const int n = h->Ns;
+    if (n != kStructNs) return false;
+    SStructT<double>& d = out->d;
+    const double a4 = 4.0 - h->m0;
+    double q = 1.0;
+    for (int s = 0; s < n; ++s) {
+        const double om = h->omega[s], dd = a4 * om + 1.0, ee = a4 * om - 1.0;
+        d.w[s] = std::sqrt(om);
+        d.rw[s] = std::sqrt(om) / dd;
+        d.f[s] = ee / dd;
+        if (s > 0) q *= -ee / dd;
+        d.q[s] = q;
+        d.wi[s] = 1.0 / std::sqrt(om);
+        d.adiag[s] = a4 - 1.0 / om;
+        d.wi2s[s] = ((s & 1) ? -2.0 : 2.0) / std::sqrt(om);
+    }
+    const double d0 = a4 * h->omega[0] + 1.0, e0 = a4 * h->omega[0] - 1.0;
+    const double ms[2] = {m1, m2};
+    for (int c = 0; c < 2; ++c) {
+        d.m[c] = ms[c];
+        d.me0[c] = ms[c] * e0;
+        d.cu[c] = 1.0 / (d0 - ms[c] * e0 * d.q[n - 1]);
+        d.au[c] = 1.0 / (1.0 + ms[c]);
+    }
+    SStructT<float>& f = out->f;
+    for (int s = 0; s < n; ++s) {
+        f.w[s] = (float)d.w[s], f.rw[s] = (float)d.rw[s], f.f[s] = (float)d.f[s], f.q[s] = (float)d.q[s];
+        f.wi[s] = (float)d.wi[s], f.adiag[s] = (float)d.adiag[s], f.wi2s[s] = (float)d.wi2s[s];
+    }
+    for (int c = 0; c < 2; ++c) {
+        f.m[c] = (float)d.m[c], f.me0[c] = (float)d.me0[c], f.cu[c] = (float)d.cu[c], f.au[c] = (float)d.au[c];
+    }
+    return true;
+}
+
+void set_sop(HopArgs& a, const SCoef* c, int sop) {
+    if (!c->has_st) {
+        a.sop = SOP_DENSE;
+        return;
+    }
+    a.sop = sop;
+    a.sc = c->st;
+}
+
 const SCoef* get_coef(odwf_s* h, double m1, double m2) {
     auto key = std::make_pair(m1, m2);
     auto it = h->coefs.find(key);
@@ -188,6 +233,7 @@ const SCoef* get_coef(odwf_s* h, double m1, double m2) {
         return nullptr;
     }
     SCoef c;
+    c.has_st = !h->dense_s && struct_host(h, m1, m2, &c.st);
     if (cudaMalloc(&c.dev, sizeof(double) * host.size()) != cudaSuccess) {
         set_err(h, ODWF_ENOMEM, "cudaMalloc coefficients");
         return nullptr;
@@ -330,6 +376,7 @@ int odwf_create(odwf_t** out, const int dims[4], int Ns, double m0, const double
     if (!rc) rc = cuda_check(h, cudaMemset(h->fault, 0, sizeof(unsigned int)), "memset fault");
     if (const char* e = std::getenv("ODWF_STAGED")) h->staged = (e[0] == '1') ? 1 : 0;
     if (const char* e = std::getenv("ODWF_TEST_WAIT_CYCLES")) h->wait_cycles = std::atoll(e);
+    if (const char* e = std::getenv("ODWF_DENSE_S")) h->dense_s = (e[0] == '1');
     if (!rc) rc = cuda_check(h, cudaMallocHost((void**)&h->fault_host, sizeof(unsigned int)), "cudaMallocHost fault");
     if (!rc) *h->fault_host = 0u;
     if (!rc) rc = cuda_check(h, cudaMemset(h->state, 0, sizeof(CGState)), "memset state");
@@ -421,6 +468,7 @@ int apply_dt_parity(odwf_s* h, int stg, const SCoef* c, bool dag, int parity, co
     a.own_scale = own_scale;
     a.out_scale = out_scale;
     a.mown = c->dev + (size_t)(dag ? 4 : 0) * h->Ns * h->Ns;
+    set_sop(a, c, dag ? (SOP_A | SOP_T) : SOP_A);
     a.c_hop = -0.5;
     a.g5 = dag ? (G5_HOP_IN | G5_OWN_IN | G5_OUT) : 0;
     return launch_hop(h, stg, parity, false, true, true, EPI_STORE, a, st);

@@ -180,7 +180,8 @@ __device__ void su3_mul4(const double* u, const double* v, double* w) {
 
 template <int MU>
 __device__ void force_link(const double* chi_self, const double* chi_nb, const int* nbr, const double* links,
-                           const int* lexof, int par, int cb, int Ns, double sgnk, double* F, int V) {
+                           const int* lexof, int par, int cb, int Ns, double sgnk, double* F, int V, double coef,
+                           int accumulate) {
     const int n = nbr[(size_t)cb * 8 + MU];
     double u[18];
     {
@@ -238,12 +239,16 @@ __device__ void force_link(const double* chi_self, const double* chi_nb, const i
     im[7] = (zi(0, 0) + zi(1, 1) - 2.0 * zi(2, 2)) / sqrt(3.0);  // lambda8
     const int lex = lexof[cb];
     double* out = F + ((size_t)MU * V + lex) * 8;
-    for (int a8 = 0; a8 < 8; ++a8) out[a8] = -0.25 * sgnk * im[a8];
+    for (int a8 = 0; a8 < 8; ++a8) {
+        const double f = -0.25 * sgnk * im[a8];
+        out[a8] = accumulate ? fma(coef, f, out[a8]) : f;
+    }
 }
 
+// F^a_mu(x) written (accumulate = 0) or added as F += coef * F^a_mu(x) (accumulate = 1: a momentum update)
 __global__ void k_force(const double* e, const double* o, const int* nbr_e, const int* nbr_o, const double* lk_e,
                         const double* lk_o, const int* lex_e, const int* lex_o, int Vh, int Ns, double sgnk,
-                        double* F) {
+                        double* F, double coef, int accumulate) {
     const int total = 2 * Vh * 4;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
         const int mu = i % 4;
@@ -256,10 +261,10 @@ __global__ void k_force(const double* e, const double* o, const int* nbr_e, cons
         const double* lk = par ? lk_o : lk_e;
         const int* lx = par ? lex_o : lex_e;
         switch (mu) {
-            case 0: force_link<0>(self, nb, nbr, lk, lx, par, cb, Ns, sgnk, F, 2 * Vh); break;
-            case 1: force_link<1>(self, nb, nbr, lk, lx, par, cb, Ns, sgnk, F, 2 * Vh); break;
-            case 2: force_link<2>(self, nb, nbr, lk, lx, par, cb, Ns, sgnk, F, 2 * Vh); break;
-            default: force_link<3>(self, nb, nbr, lk, lx, par, cb, Ns, sgnk, F, 2 * Vh); break;
+            case 0: force_link<0>(self, nb, nbr, lk, lx, par, cb, Ns, sgnk, F, 2 * Vh, coef, accumulate); break;
+            case 1: force_link<1>(self, nb, nbr, lk, lx, par, cb, Ns, sgnk, F, 2 * Vh, coef, accumulate); break;
+            case 2: force_link<2>(self, nb, nbr, lk, lx, par, cb, Ns, sgnk, F, 2 * Vh, coef, accumulate); break;
+            default: force_link<3>(self, nb, nbr, lk, lx, par, cb, Ns, sgnk, F, 2 * Vh, coef, accumulate); break;
         }
     }
 }
@@ -587,22 +592,29 @@ extern "C" int eofa_action(odwf_t* h, const eofa_term* t, const void* phi, doubl
     return src;
 }
 
-extern "C" int eofa_force(odwf_t* h, const eofa_term* t, const void* phi, double* F, const odwf_solve_opts* opts,
-                          odwf_solve_stats* stats, void* stream) {
-    if (!h || !phi || !F) return set_err(h, ODWF_EINVAL, "null argument");
-    if (!h->have_gauge) return set_err(h, ODWF_EINVAL, "odwf_set_gauge has not been called");
+namespace odwf {
+// F (accumulate = 0) or F += coef * F_term (accumulate = 1) for one term; one H_T(m3, m4) solve
+int term_force(odwf_s* h, const eofa_term* t, const void* phi, double* F, double coef, int accumulate,
+               const odwf_solve_opts* opts, odwf_solve_stats* stats, cudaStream_t st) {
     int rc = check_term(h, t);
     if (rc) return rc;
-    cudaStream_t st = (cudaStream_t)stream;
     const int src = term_solve(h, t, t->m3, t->m4, phi, opts, stats, st);
     if (src != ODWF_OK && src != ODWF_ENOCONV) return src;
     const double sgnk = (t->chirality < 0 ? 1.0 : -1.0) * term_k(t);
     const int total = 2 * h->Vh * 4;
     k_force<<<grid_for(h, total, 128), 128, 0, st>>>((const double*)h->ws.x_e, (const double*)h->ws.x_o, h->nbr[0],
                                                      h->nbr[1], h->U64[0], h->U64[1], h->lexof[0], h->lexof[1], h->Vh,
-                                                     h->Ns, sgnk, F);
+                                                     h->Ns, sgnk, F, coef, accumulate);
     if ((rc = cuda_check(h, cudaGetLastError(), "k_force"))) return rc;
     return src;
+}
+}  // namespace odwf
+
+extern "C" int eofa_force(odwf_t* h, const eofa_term* t, const void* phi, double* F, const odwf_solve_opts* opts,
+                          odwf_solve_stats* stats, void* stream) {
+    if (!h || !phi || !F) return set_err(h, ODWF_EINVAL, "null argument");
+    if (!h->have_gauge) return set_err(h, ODWF_EINVAL, "odwf_set_gauge has not been called");
+    return term_force(h, t, phi, F, 1.0, 0, opts, stats, (cudaStream_t)stream);
 }
 
 extern "C" int eofa_term_spectrum(odwf_t* h, const eofa_term* t, const void* v0, int n_iter, double* lo, double* hi,

@@ -226,6 +226,126 @@ __device__ __forceinline__ void s_mix2(const R* mp, const R* sh_site, int s, int
     for (int k = 0; k < 24; ++k) out[k] = accumulate ? out[k] + acc[k] : acc[k];
 }
 
+// ---- structured fifth-dimension products (see SStruct), Ns = kStructNs ----------------------------
+// After the hop, each (site, s) thread stores its 24-real row; then the thread of slice j < 12 of
+// the site takes complex component j of all Ns rows (one column, re and im), applies A or A^{-1}
+// of that component's chirality by the O(Ns) recurrence in registers, and writes the column back;
+// finally every thread reads its own row again. The coefficients are indexed by the step of the
+// recurrence only (compile-time, unrolled), so in a kernel whose arguments are the SStruct by value
+// they are constant-bank operands of the FMAs.
+template <typename R>
+__device__ __forceinline__ const SStructT<R>& sst_of(const SStruct& s);
+template <>
+__device__ __forceinline__ const SStructT<float>& sst_of<float>(const SStruct& s) { return s.f; }
+template <>
+__device__ __forceinline__ const SStructT<double>& sst_of<double>(const SStruct& s) { return s.d; }
+
+// Shared-memory geometry of the structured staging rows: row stride kSRow reals, site stride kSSite
+// reals (16 x 28 + 16 floats: the column loads of the 24 active lanes of a warp and the 16-byte row
+// stores are both free of bank conflicts beyond their minimum wavefront count).
+template <typename R>
+constexpr int kSRow = sizeof(R) == 4 ? 28 : 26;
+template <typename R>
+constexpr int kSSite = kStructNs * kSRow<R> + (sizeof(R) == 4 ? 16 : 4);
+
+__device__ __forceinline__ void pair_ld(const float* p, float& a, float& b) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    a = t.x, b = t.y;
+}
+__device__ __forceinline__ void pair_ld(const double* p, double& a, double& b) {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    a = t.x, b = t.y;
+}
+__device__ __forceinline__ void pair_st(float* p, float a, float b) { *reinterpret_cast<float2*>(p) = make_float2(a, b); }
+__device__ __forceinline__ void pair_st(double* p, double a, double b) {
+    *reinterpret_cast<double2*>(p) = make_double2(a, b);
+}
+
+// A^{-1} = W (1 + L) B^{-1} W on one complex column (x = xr + i xi) in recurrence order:
+//   p_0 = 0, p_s = (omega_s^{1/2}/d_s) x_s - (e_s/d_s) p_{s-1};  B y = W x with y_s = p_s + q_s u,
+//   u = y_0 = (omega_0^{1/2} x_0 + m e_0 p_{N-1}) / (d_0 - m e_0 q_{N-1});
+//   out_s = omega_s^{1/2} (y_s + y_{s-1}) (s >= 1),  out_0 = omega_0^{1/2} (y_0 - m y_{N-1}).
+template <typename R, int N>
+__device__ __forceinline__ void s_ainv_col(const SStructT<R>& k, int c, R* xr, R* xi) {
+    const R z0r = k.w[0] * xr[0], z0i = k.w[0] * xi[0];
+    xr[0] = 0, xi[0] = 0;
+#pragma unroll
+    for (int s = 1; s < N; ++s) {
+        xr[s] = fma(-k.f[s], xr[s - 1], k.rw[s] * xr[s]);
+        xi[s] = fma(-k.f[s], xi[s - 1], k.rw[s] * xi[s]);
+    }
+    const R me0 = c ? k.me0[1] : k.me0[0], cu = c ? k.cu[1] : k.cu[0], m = c ? k.m[1] : k.m[0];
+    const R ur = cu * fma(me0, xr[N - 1], z0r), ui = cu * fma(me0, xi[N - 1], z0i);
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+        xr[s] = fma(k.q[s], ur, xr[s]);
+        xi[s] = fma(k.q[s], ui, xi[s]);
+    }
+    const R ylr = xr[N - 1], yli = xi[N - 1];
+#pragma unroll
+    for (int s = N - 1; s >= 1; --s) {
+        xr[s] = k.w[s] * (xr[s] + xr[s - 1]);
+        xi[s] = k.w[s] * (xi[s] + xi[s - 1]);
+    }
+    xr[0] = k.w[0] * fma(-m, ylr, xr[0]);
+    xi[0] = k.w[0] * fma(-m, yli, xi[0]);
+}
+
+// A = (4 - m0 - 1/omega) + 2 W^{-1} (1 + L)^{-1} W^{-1} on one complex column in recurrence order:
+//   z = W^{-1} x, p_0 = 0, p_s = z_s - p_{s-1}, (1 + L)^{-1} z = p + (-1)^s u, u = (z_0 + m p_{N-1})/(1 + m).
+template <typename R, int N>
+__device__ __forceinline__ void s_a_col(const SStructT<R>& k, int c, R* xr, R* xi) {
+    const R z0r = k.wi[0] * xr[0], z0i = k.wi[0] * xi[0];
+    R pr = 0, pi = 0;
+    xr[0] = k.adiag[0] * xr[0], xi[0] = k.adiag[0] * xi[0];
+#pragma unroll
+    for (int s = 1; s < N; ++s) {
+        pr = fma(k.wi[s], xr[s], -pr);
+        pi = fma(k.wi[s], xi[s], -pi);
+        xr[s] = fma(k.wi[s], pr + pr, k.adiag[s] * xr[s]);
+        xi[s] = fma(k.wi[s], pi + pi, k.adiag[s] * xi[s]);
+    }
+    const R m = c ? k.m[1] : k.m[0], au = c ? k.au[1] : k.au[0];
+    const R ur = au * fma(m, pr, z0r), ui = au * fma(m, pi, z0i);
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+        xr[s] = fma(k.wi2s[s], ur, xr[s]);
+        xi[s] = fma(k.wi2s[s], ui, xi[s]);
+    }
+}
+
+// The column pass of thread j of one site (site: its staged rows, row stride rs); threads j >= 12
+// have no column. P_+ components (j < 6) run forward in s and P_- ones backward, both reversed for
+// a transposed operator.
+template <typename R, int N>
+__device__ __forceinline__ void s_struct_col(const SStruct& sc, int sop, R* site, int rs, int j) {
+    if (j >= 12) return;
+    const SStructT<R>& k = sst_of<R>(sc);
+    const int c = j < 6 ? 0 : 1;
+    const bool rev = (c == 1) != ((sop & SOP_T) != 0);
+    R* p0 = site + 2 * j + (rev ? (N - 1) * rs : 0);
+    const int step = rev ? -rs : rs;
+    R xr[N], xi[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) pair_ld(p0 + q * step, xr[q], xi[q]);
+    if ((sop & 3) == SOP_AINV) s_ainv_col<R, N>(k, c, xr, xi);
+    else s_a_col<R, N>(k, c, xr, xi);
+#pragma unroll
+    for (int q = 0; q < N; ++q) pair_st(p0 + q * step, xr[q], xi[q]);
+}
+
+// out = [out +] the staged row at p (24 reals, 16-byte aligned)
+template <typename R>
+__device__ __forceinline__ void row24_load(const R* p, R* out, bool accumulate) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        R t[4];
+        row4_load(p + 4 * q, t);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) out[4 * q + i] = accumulate ? out[4 * q + i] + t[i] : t[i];
+    }
+}
+
 // ---- fifth-dimension mixing on the tensor cores, Ns = 16 -----------------------------------------
 // With Ns = 16 a warp holds exactly two sites (its own 32 (site, s) threads), so the mixing of those
 // two sites is warp-local: per chirality c the product D = A_c B of the 16 x 16 matrix A_c with the

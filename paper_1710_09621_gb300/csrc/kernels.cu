@@ -277,7 +277,9 @@ constexpr bool kLeanK1 = true;
 template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN>
 constexpr bool kLeanHop = kLeanK1 && ST == ST_FLOAT && HOP && MIXHOP && !OWN && !MIXOWN;
 
-template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI, bool WS>
+// SN > 0 (= kStructNs = Ns): the fifth-dimension product is the structured O(Ns) recurrence of
+// a.sop (s_struct_col) instead of the dense Ns x Ns matrix.
+template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI, bool WS, int SN>
 __device__ __forceinline__ void hop_body(const HopArgs& a) {
     using S = Store<ST>;
     using R = typename S::R;
@@ -285,30 +287,35 @@ __device__ __forceinline__ void hop_body(const HopArgs& a) {
     const int Ns = a.Ns;
     const int s = threadIdx.x, ls = threadIdx.y, spb = blockDim.y;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
-    // FP32 arithmetic at Ns = 16: warp-local tensor-core s-mixing, with its A-fragment tables first
-    // in shared memory; otherwise FMA s-mixing from the matrices mh / mo
-    constexpr bool kTC = std::is_same<R, float>::value && (MIXHOP || MIXOWN) && !kLeanHop<ST, HOP, MIXHOP, OWN, MIXOWN>;
+    constexpr bool STRUCT = SN > 0;
+    // FP32 arithmetic at Ns = 16 (dense form): warp-local tensor-core s-mixing, with its A-fragment
+    // tables first in shared memory; otherwise FMA s-mixing from the matrices mh / mo
+    constexpr bool kTC = !STRUCT && std::is_same<R, float>::value && (MIXHOP || MIXOWN) &&
+                         !kLeanHop<ST, HOP, MIXHOP, OWN, MIXOWN>;
     const bool tc = kTC && Ns == 16;
     // staging row stride: 24 reals for the tensor-core mixing (its fragment loads are laid out for
-    // it), the padded stride for the FMA mixing
-    const int rst = tc ? 24 : kRowStride<R>;
-    const int sst = Ns * rst;
+    // it), the padded stride for the FMA mixing, the structured geometry for the column pass
+    const int rst = STRUCT ? kSRow<R> : (tc ? 24 : kRowStride<R>);
+    const int sst = STRUCT ? kSSite<R> : Ns * rst;
+    constexpr int NMAT = STRUCT ? 0 : 1;
     uint32_t* afr_h = reinterpret_cast<uint32_t*>(smem_raw);
     uint32_t* afr_o = afr_h + (tc && MIXHOP ? kAfrag16Words : 0);
     R* mh = reinterpret_cast<R*>(afr_o + (tc && MIXOWN ? kAfrag16Words : 0));
-    R* mo = mh + (MIXHOP ? 2 * Ns * Ns : 0);
-    R* sh = mo + (MIXOWN ? 2 * Ns * Ns : 0);
+    R* mo = mh + (MIXHOP ? NMAT * 2 * Ns * Ns : 0);
+    R* sh = mo + (MIXOWN ? NMAT * 2 * Ns * Ns : 0);
     const int lane = tid & 31, warp = tid >> 5;
     constexpr bool REDUCE = (EPI != EPI_STORE);
 
     if (a.state != nullptr && EPI != EPI_STORE_NORM && EPI != EPI_RESID) {
         if (((volatile CGState*)a.state)->flag != FLAG_RUN) return;
     }
-    for (int i = tid; i < 2 * Ns * Ns; i += nth) {
-        // interleaved chirality pairs: (M_+, M_-)[s' Ns + s] side by side, one load per s'
-        const int j = i < Ns * Ns ? 2 * i : 2 * (i - Ns * Ns) + 1;
-        if (MIXHOP) mh[j] = (R)a.mhop[i];
-        if (MIXOWN) mo[j] = (R)a.mown[i];
+    if constexpr (!STRUCT) {
+        for (int i = tid; i < 2 * Ns * Ns; i += nth) {
+            // interleaved chirality pairs: (M_+, M_-)[s' Ns + s] side by side, one load per s'
+            const int j = i < Ns * Ns ? 2 * i : 2 * (i - Ns * Ns) + 1;
+            if (MIXHOP) mh[j] = (R)a.mhop[i];
+            if (MIXOWN) mo[j] = (R)a.mown[i];
+        }
     }
     if constexpr (kTC) {
         if (tc) {
@@ -358,7 +365,14 @@ __device__ __forceinline__ void hop_body(const HopArgs& a) {
                 for (int k = 0; k < 24; ++k) v[k] = fma(aown, ow[k], v[k]);
             }
         }
-        if (MIXHOP) {
+        if (MIXHOP && STRUCT) {
+            R* row = sh + ls * sst + s * rst;
+            row24_store(row, v);
+            site_barrier<WS>();
+            if constexpr (STRUCT) s_struct_col<R, (STRUCT ? SN : 1)>(a.sc, a.sop, sh + ls * sst, rst, s);
+            site_barrier<WS>();
+            row24_load(row, v, false);
+        } else if (MIXHOP) {
             row24_store(sh + ls * sst + s * rst, v);
             if constexpr (kTC) {
                 if (tc) {
@@ -373,7 +387,15 @@ __device__ __forceinline__ void hop_body(const HopArgs& a) {
                 s_mix2(mh, sh + ls * sst, s, Ns, v, false, rst);
             }
         }
-        if (MIXOWN) {
+        if (MIXOWN && STRUCT) {
+            if (MIXHOP) site_barrier<WS>();
+            R* row = sh + ls * sst + s * rst;
+            row24_store(row, ow);
+            site_barrier<WS>();
+            if constexpr (STRUCT) s_struct_col<R, (STRUCT ? SN : 1)>(a.sc, a.sop, sh + ls * sst, rst, s);
+            site_barrier<WS>();
+            row24_load(row, v, true);
+        } else if (MIXOWN) {
             if (MIXHOP) {
                 if (tc) __syncwarp();
                 else site_barrier<WS>();
@@ -721,17 +743,17 @@ size_t staged_smem(int Ns, int spb, bool mixhop, bool mixown) {
            (size_t)G::nslots(spb) * (G::slot_bytes(Ns) + G::scale_bytes(Ns));
 }
 
-template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI, bool WS>
+template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI, bool WS, int SN = 0>
 __global__ void __launch_bounds__(256) k_hop(HopArgs a) {
-    hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS>(a);
+    hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS, SN>(a);
 }
 
 // Register-capped copy for the FP32 hop-then-mix variant (K1, K1^dag): at most 64 registers (4 CTAs
 // of 256 or 8 of 128 threads per SM) costs it 8 bytes of spill and buys resident warps for its
 // latency-bound neighbour gathers; the other variants (which would spill more) keep k_hop.
-template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI, bool WS>
+template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI, bool WS, int SN = 0>
 __global__ void __launch_bounds__(256, 4) k_hop_lean(HopArgs a) {
-    hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS>(a);
+    hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS, SN>(a);
 }
 
 
@@ -742,21 +764,22 @@ __global__ void __launch_bounds__(256, 4) k_hop_lean(HopArgs a) {
 template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI, bool WS>
 __global__ void __launch_bounds__(256) k_hop_multi(const HopArgs* __restrict__ args) {
     __shared__ HopArgs sa;
-    hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS>(stage_args(args, &sa));
+    hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS, 0>(stage_args(args, &sa));
 }
 
 template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI, bool WS>
 __global__ void __launch_bounds__(256, 4) k_hop_multi_lean(const HopArgs* __restrict__ args) {
     __shared__ HopArgs sa;
-    hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS>(stage_args(args, &sa));
+    hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS, 0>(stage_args(args, &sa));
 }
 
 // the per-thread-gather kernel of a variant, single system and several systems; WS (Ns divides
-// 32) selects warp-level instead of CTA-wide synchronisation of the staged rows
-template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI, bool WS>
+// 32) selects warp-level instead of CTA-wide synchronisation of the staged rows; SN the
+// structured fifth-dimension product (single-system kernels, Ns = kStructNs)
+template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI, bool WS, int SN = 0>
 constexpr auto hop_kernel() {
-    if constexpr (kLeanHop<ST, HOP, MIXHOP, OWN, MIXOWN>) return k_hop_lean<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS>;
-    else return k_hop<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS>;
+    if constexpr (kLeanHop<ST, HOP, MIXHOP, OWN, MIXOWN>) return k_hop_lean<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS, SN>;
+    else return k_hop<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS, SN>;
 }
 template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI, bool WS>
 constexpr auto hop_multi_kernel() {
@@ -821,11 +844,15 @@ static int grid_for_mode(const odwf_s* h, int mode, int occ, int groups, bool re
 template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
 struct KernelPick {
     static constexpr bool CAN_STAGE = HOP && ST != ST_DOUBLE;
-    // kind: 0 plain single, 1 plain multi, 2 staged single, 3 staged multi
+    static constexpr bool CAN_STRUCT = MIXHOP || MIXOWN;
+    // kind: 0 plain single, 1 plain multi, 2 staged single, 3 staged multi, 4 structured single
     static const void* fn(int kind, bool ws) {
         if constexpr (CAN_STAGE) {
             if (kind == 2) return (const void*)k_hop_staged<ST, MIXHOP, OWN, MIXOWN, EPI>;
             if (kind == 3) return (const void*)k_hop_staged_multi<ST, MIXHOP, OWN, MIXOWN, EPI>;
+        }
+        if constexpr (CAN_STRUCT) {
+            if (kind == 4) return (const void*)hop_kernel<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, true, kStructNs>();
         }
         if (ws)
             return kind == 1 ? (const void*)hop_multi_kernel<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, true>()
@@ -844,11 +871,12 @@ static int occupancy(odwf_s* h, int kind, size_t* smem_out) {
     if (std::is_same<R, float>::value && Ns == 16 && !kLeanHop<ST, HOP, MIXHOP, OWN, MIXOWN>)
         smem += sizeof(uint32_t) * kAfrag16Words * (MIXHOP + MIXOWN);
     if constexpr (ST != ST_DOUBLE) {
-        if (kind >= 2) smem = staged_smem<ST>(Ns, spb, MIXHOP, MIXOWN);
+        if (kind == 2 || kind == 3) smem = staged_smem<ST>(Ns, spb, MIXHOP, MIXOWN);
     }
+    if (kind == 4) smem = sizeof(R) * (size_t)spb * kSSite<R>;
     *smem_out = smem;
-    static int occ_cache[4][kMaxNs + 1] = {{0}};
-    static bool attr_set[4][2] = {{false, false}, {false, false}, {false, false}, {false, false}};
+    static int occ_cache[5][kMaxNs + 1] = {{0}};
+    static bool attr_set[5][2] = {{false, false}, {false, false}, {false, false}, {false, false}, {false, false}};
     const bool ws = warp_sites(Ns);
     const void* fn = KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::fn(kind, ws);
     if (!attr_set[kind][ws]) {
@@ -905,7 +933,10 @@ static int launch_one(odwf_s* h, int parity, HopArgs a, cudaStream_t st) {
         mode = tuned->second.first;
         stg = KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::CAN_STAGE && staged_geom_ok(h, ST) && tuned->second.second;
     }
-    const int occ = occupancy<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(h, stg ? 2 : 0, &smem);
+    // the structured fifth-dimension product: single-system per-thread-gather kernels at Ns = kStructNs
+    const bool sn = KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::CAN_STRUCT && !stg && Ns == kStructNs &&
+                    a.sop != SOP_DENSE;
+    const int occ = occupancy<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(h, stg ? 2 : (sn ? 4 : 0), &smem);
     const int groups = (h->Vh + spb - 1) / spb;
     const int grid = grid_for_mode(h, mode, occ, groups, EPI != EPI_STORE);
     hop_fill(h, ST, parity, a, EPI != EPI_STORE);
@@ -917,6 +948,12 @@ static int launch_one(odwf_s* h, int parity, HopArgs a, cudaStream_t st) {
         if (stg) {
             h->staged_used = true;
             k_hop_staged<ST, MIXHOP, OWN, MIXOWN, EPI><<<grid, dim3(Ns, spb), smem, st>>>(a);
+            plain = false;
+        }
+    }
+    if constexpr (KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::CAN_STRUCT) {
+        if (sn) {
+            hop_kernel<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, true, kStructNs>()<<<grid, dim3(Ns, spb), smem, st>>>(a);
             plain = false;
         }
     }
@@ -990,11 +1027,12 @@ int launch_hop_own_cgb(odwf_s* h, int storage, HopArgs a, cudaStream_t st) {
 }
 
 int launch_smix(odwf_s* h, int storage, const void* in, void* out, const double* mt, double, cudaStream_t st,
-                const float* in_scale, float* out_scale) {
+                const float* in_scale, float* out_scale, const SCoef* c, int sop) {
     HopArgs a{};
     a.own = in;
     a.out = out;
     a.mown = mt;
+    if (c && sop != SOP_DENSE) set_sop(a, c, sop);
     a.own_scale = in_scale;
     a.out_scale = out_scale;
     switch (storage) {
@@ -1340,6 +1378,7 @@ int autotune_storage(odwf_s* h, int stg, const SCoef* c, cudaStream_t st, std::v
         }
         a.mhop = c->dev + (size_t)2 * NN;
         a.mown = c->dev;
+        set_sop(a, c, v.mixhop ? SOP_AINV : SOP_A);
         a.c_hop = v.mixhop ? 1.0 : -0.25;
         a.x = w.xi;
         a.x_scale = w.xi_s;

@@ -685,6 +685,7 @@ struct odwf_net_s {
     bool prepped = false;
     double cm1 = -1, cm2 = -1;
     double* mats = nullptr;  // transposed A^{-1} (2 Ns^2) then A^{-T} (2 Ns^2), FP64
+    SCoef sc{};              // structured form of the same (for the s-mixing kernel; sc.dev unused)
     // FP32 half fields: u (even), v[C] (odd), t (even), gy (even), gh[C] (odd), delta (even)
     float* f[8] = {nullptr};
     float* sf[2] = {nullptr, nullptr};  // preconditioned solve: p (even), t (odd)
@@ -720,6 +721,7 @@ int net_set_masses(odwf_net_s* n, double m1, double m2) {
     if (rc) return rc;
     if (cudaMemcpy(n->mats, m.data(), sizeof(double) * 4 * NN, cudaMemcpyHostToDevice) != cudaSuccess)
         return net_err(n, ODWF_ECUDA, "copy mixing matrices");
+    n->sc.has_st = !n->h->dense_s && struct_host(n->h, m1, m2, &n->sc.st);
     n->cm1 = m1;
     n->cm2 = m2;
     return ODWF_OK;
@@ -797,7 +799,9 @@ int net_layer(odwf_net_s* n, int parity, int cin, int cout, const float* const* 
 
 // s-mixing of an FP32 half field with a transposed matrix pair (uses the library's s-mix kernel)
 int net_smix(odwf_net_s* n, const float* in, float* out, const double* mt, cudaStream_t st) {
-    return launch_smix(n->h, ST_FLOAT, in, out, mt, 1.0, st);
+    const bool transposed = (mt != n->mats);  // n->mats + 2 Ns^2 holds A^{-T}
+    return launch_smix(n->h, ST_FLOAT, in, out, mt, 1.0, st, nullptr, nullptr, &n->sc,
+                       transposed ? (SOP_AINV | SOP_T) : SOP_AINV);
 }
 
 // M r (adjoint = 0) or M^dag r (adjoint = 1) on FP32 even fields; uses f[0] (u), f[1..2] (v / gh)
@@ -1127,6 +1131,7 @@ int residual64(odwf_s* h, const SCoef* c, const void* bh, const void* x, void* t
     a.in = x;
     a.out = tmp;
     a.mhop = coef_mat(c, 2, h->Ns);
+    set_sop(a, c, SOP_AINV);
     a.c_hop = 1.0;
     int rc = launch_hop(h, ST_DOUBLE, 1, true, false, false, EPI_STORE, a, st);
     if (rc) return rc;
@@ -1135,6 +1140,7 @@ int residual64(odwf_s* h, const SCoef* c, const void* bh, const void* x, void* t
     b.own = x;
     b.out = out;
     b.mown = coef_mat(c, 0, h->Ns);
+    set_sop(b, c, SOP_A);
     b.c_hop = -0.25;
     b.x = const_cast<void*>(bh);
     b.slot = slot;
@@ -1160,7 +1166,8 @@ int schur_start(odwf_s* h, const SCoef* c, const void* b, double* bnorm2, double
     if ((rc = launch_pack5(h, (const double*)b, w.b_e, w.b_o, ST_DOUBLE, 1, st))) return rc;
     if ((rc = launch_norm2(h, w.b_e, ST_DOUBLE, nullptr, 0, st))) return rc;
     if ((rc = launch_norm2(h, w.b_o, ST_DOUBLE, nullptr, 1, st))) return rc;
-    if ((rc = launch_smix(h, ST_DOUBLE, w.b_o, w.t64, coef_mat(c, 2, h->Ns), 1.0, st))) return rc;
+    if ((rc = launch_smix(h, ST_DOUBLE, w.b_o, w.t64, coef_mat(c, 2, h->Ns), 1.0, st, nullptr, nullptr, c, SOP_AINV)))
+        return rc;
     {
         HopArgs a{};
         a.in = w.t64;
@@ -1192,9 +1199,11 @@ int schur_finish(odwf_s* h, const SCoef* c, void* x, double bnorm2, double* res,
     a.a_own = 1.0;
     a.c_hop = 0.5;
     a.mhop = coef_mat(c, 2, h->Ns);
+    set_sop(a, c, SOP_AINV);
     if ((rc = launch_hop(h, ST_DOUBLE, 1, true, true, false, EPI_STORE, a, st))) return rc;
     HopArgs r2{};
     r2.mown = coef_mat(c, 0, h->Ns);
+    set_sop(r2, c, SOP_A);
     r2.c_hop = -0.5;
     r2.in = w.x_o;
     r2.own = w.x_e;
@@ -1220,6 +1229,7 @@ int schur32(odwf_s* h, const SCoef* c, const float* in, float* tmp, float* out, 
     a.in = in;
     a.out = tmp;
     a.mhop = coef_mat(c, dag ? 6 : 2, h->Ns);
+    set_sop(a, c, dag ? (SOP_AINV | SOP_T) : SOP_AINV);
     a.c_hop = 1.0;
     a.g5 = dag ? G5_HOP_IN : 0;
     int rc = launch_hop(h, ST_FLOAT, 1, true, false, false, EPI_STORE, a, st);
@@ -1229,6 +1239,7 @@ int schur32(odwf_s* h, const SCoef* c, const float* in, float* tmp, float* out, 
     b2.own = in;
     b2.out = out;
     b2.mown = coef_mat(c, dag ? 4 : 0, h->Ns);
+    set_sop(b2, c, dag ? (SOP_A | SOP_T) : SOP_A);
     b2.c_hop = -0.25;
     b2.g5 = dag ? (G5_OWN_IN | G5_OUT) : 0;
     return launch_hop(h, ST_FLOAT, 0, false, true, true, EPI_STORE, b2, st);
@@ -1294,6 +1305,7 @@ extern "C" int eofa_solve_learned(odwf_t* h, odwf_net_t* n, double m1, double m2
                 a.in = z;
                 a.out = t;
                 a.mhop = coef_mat(c, 2, h->Ns);
+                set_sop(a, c, SOP_AINV);
                 a.c_hop = 1.0;
                 a.state = h->state;
                 if ((rc = launch_hop(h, ST_FLOAT, 1, true, false, false, EPI_STORE, a, st))) return rc;
@@ -1301,6 +1313,7 @@ extern "C" int eofa_solve_learned(odwf_t* h, odwf_net_t* n, double m1, double m2
                 b2.in = t;
                 b2.own = z;
                 b2.mown = coef_mat(c, 0, h->Ns);
+                set_sop(b2, c, SOP_A);
                 b2.c_hop = -0.25;
                 b2.x = xi;
                 b2.r = rho;

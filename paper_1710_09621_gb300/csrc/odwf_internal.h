@@ -55,6 +55,37 @@ enum : int {
 // gamma_5 flags of the generic hopping kernel
 enum : int { G5_HOP_IN = 1, G5_OWN_IN = 2, G5_OUT = 4 };
 
+// ---- structured fifth-dimension operators -------------------------------------------------------
+// With B = (4 - m0) omega (1 + L) + (1 - L), a cyclic bidiagonal matrix, and W = omega^{1/2}:
+//   A      = (4 - m0) + M = (4 - m0 - 1/omega) + 2 W^{-1} (1 + L)^{-1} W^{-1}
+//   A^{-1} = W (1 + L) B^{-1} W
+// (M = W^{-1} (1 - L)(1 + L)^{-1} W^{-1}). Both apply in O(Ns) per spinor component by one forward
+// recurrence in s plus the cyclic corner term. For chirality P_+ the recurrence runs forward in s
+// (L_+ is lower bidiagonal with the corner -m1); A_-(m2) = R5 A_+(m2) R5 and A_+(m)^T = A_-(m), so
+// P_- components and transposed operators run the same recurrence on the reversed s index. Since
+// omega is R5-symmetric, the coefficients below, indexed by the step sigma of the recurrence, are
+// the same in both orientations; only the mass terms depend on the chirality.
+constexpr int kStructNs = 16;  // Ns of the structured kernels (other Ns use the dense Ns x Ns mixing)
+enum : int { SOP_DENSE = 0, SOP_A = 1, SOP_AINV = 2, SOP_T = 4 };
+template <typename R>
+struct SStructT {
+    R w[kStructNs];      // omega^{1/2}
+    R rw[kStructNs];     // omega^{1/2} / d,  d = (4 - m0) omega + 1 (diagonal of B)
+    R f[kStructNs];      // e / d,  e = (4 - m0) omega - 1 (sub-diagonal of B)
+    R q[kStructNs];      // prod_{i = 1..sigma} (-e_i / d_i) (homogeneous solution of B y = 0 rows 1..)
+    R wi[kStructNs];     // omega^{-1/2}
+    R adiag[kStructNs];  // 4 - m0 - 1/omega
+    R wi2s[kStructNs];   // 2 (-1)^sigma omega^{-1/2}
+    R m[2];              // mass of chirality P_+ (m1) and P_- (m2)
+    R me0[2];            // m e_0
+    R cu[2];             // 1 / (d_0 - m e_0 q_{Ns-1})
+    R au[2];             // 1 / (1 + m)
+};
+struct SStruct {
+    SStructT<double> d;
+    SStructT<float> f;
+};
+
 enum StorageKind : int { ST_DOUBLE = 0, ST_FLOAT = 1, ST_HALF = 2 };
 
 // Arguments of the generic 5D hopping kernel (one output parity). Field pointers are to the
@@ -84,6 +115,8 @@ struct HopArgs {
     int parity;          // output parity (bulk-staged kernels derive in-block neighbours from it)
     unsigned int* fault; // set to 1 if a bulk-copy wait ran out of time (never expected)
     long long wait_cycles;  // limit of the bulk-copy wait in SM clock cycles (0: the default, ~1 s)
+    int sop;             // SOP_*: structured form of the Mhop / Mown matrix (SOP_DENSE: use the matrix)
+    SStruct sc;          // its coefficients (used when sop != SOP_DENSE and Ns == kStructNs)
 };
 
 // ---- host-side handle --------------------------------------------------------------------------
@@ -93,6 +126,8 @@ struct SCoef {
     //  8 N_+ = omega^{1/2}(1 + L_+(m1)), 9 N_-, 10/11 omega^{1/2} (diagonal), 12 N_+^T, 13 N_-^T
     // "transposed" means stored as Mt[s'][s] = M[s][s'] so thread s reads consecutive words.
     double* dev = nullptr;
+    SStruct st{};        // structured coefficients of A_pm and A_pm^{-1} (Ns == kStructNs only)
+    bool has_st = false;
 };
 
 struct Workspace {
@@ -139,6 +174,7 @@ struct odwf_s {
     bool staged_used = false;             // a bulk-staged kernel ran since the fault word was last read
     long long wait_cycles = 0;            // HopArgs::wait_cycles (ODWF_TEST_WAIT_CYCLES, tests only)
     int staged = 0;                       // use the bulk-staged hop kernels where they apply (ODWF_STAGED=1)
+    bool dense_s = false;                 // dense Ns x Ns fifth-dimension products everywhere (ODWF_DENSE_S=1)
     // autotuned launch choice per kernel variant (key without the staged flag): grid mode, staged
     std::map<int, std::pair<int, int>> tune;
     // batch-solve pools: per-system workspaces, solver states, reduction buffers, kernel arguments
@@ -181,6 +217,10 @@ int ensure_workspace(odwf_s* h, int inner);
 int cuda_check(odwf_s* h, cudaError_t e, const char* what);
 const SCoef* get_coef(odwf_s* h, double m1, double m2);
 bool coef_host(const odwf_s* h, double m1, double m2, std::vector<double>& host, std::string& err);
+// structured coefficients of the mass pair (false if Ns != kStructNs)
+bool struct_host(const odwf_s* h, double m1, double m2, SStruct* out);
+// the kernel arguments' structured operator: A (SOP_A) or A^{-1} (SOP_AINV), optionally transposed
+void set_sop(HopArgs& a, const SCoef* c, int sop);
 // FP16 storage passes the per-(cb, s) scales of the three fields (ignored for FP64 / FP32)
 int apply_dt_parity(odwf_s* h, int stg, const SCoef* c, bool dag, int parity, const void* in_other,
                     const void* own, void* out, cudaStream_t st, const float* in_scale = nullptr,
@@ -191,7 +231,8 @@ int apply_dt_parity(odwf_s* h, int stg, const SCoef* c, bool dag, int parity, co
 int launch_hop(odwf_s* h, int storage, int parity, bool mixhop, bool own, bool mixown, int epi,
                HopArgs a, cudaStream_t st);
 int launch_smix(odwf_s* h, int storage, const void* in, void* out, const double* mt, double scale,
-                cudaStream_t st, const float* in_scale = nullptr, float* out_scale = nullptr);
+                cudaStream_t st, const float* in_scale = nullptr, float* out_scale = nullptr,
+                const SCoef* c = nullptr, int sop = SOP_DENSE);
 int launch_pack5(odwf_s* h, const double* lex5, void* e, void* o, int storage, int r5g5, cudaStream_t st,
                  float* e_scale = nullptr, float* o_scale = nullptr);
 int launch_unpack5(odwf_s* h, const void* e, const void* o, double* lex5, int storage, int r5g5,
@@ -212,4 +253,7 @@ void prof_begin(odwf_s* h, int key, cudaStream_t st, cudaEvent_t* a);
 void prof_end(odwf_s* h, int key, cudaStream_t st, cudaEvent_t a);
 
 // field helpers for EOFA (eofa.cu)
+// F (accumulate = 0) or F += coef F_term (accumulate = 1), F^a_mu(x) = -dS/dw^a of one EOFA term
+int term_force(odwf_s* h, const eofa_term* t, const void* phi, double* F, double coef, int accumulate,
+               const odwf_solve_opts* opts, odwf_solve_stats* stats, cudaStream_t st);
 }  // namespace odwf

@@ -62,6 +62,7 @@ static HopArgs k1_args(const Slot& s, bool dag) {
     a.out = s.f.t;
     a.out_scale = s.f.ts;
     a.mhop = mat(s.c, dag ? M_AINVT : M_AINV, s.h->Ns);
+    set_sop(a, s.c, dag ? (SOP_AINV | SOP_T) : SOP_AINV);
     a.c_hop = 1.0;
     a.g5 = dag ? G5_HOP_IN : 0;
     a.state = s.state;
@@ -77,6 +78,7 @@ static HopArgs k2a_args(const Slot& s) {
     a.own = s.f.p;
     a.own_scale = s.f.ps;
     a.mown = mat(s.c, M_AP, s.h->Ns);
+    set_sop(a, s.c, SOP_A);
     a.c_hop = -0.25;
     a.x = s.f.x;
     a.x_scale = s.f.xs;
@@ -95,6 +97,7 @@ static HopArgs k2b_args(const Slot& s) {
     a.own = s.f.r;
     a.own_scale = s.f.rs;
     a.mown = mat(s.c, M_AT, s.h->Ns);
+    set_sop(a, s.c, SOP_A | SOP_T);
     a.c_hop = -0.25;
     a.g5 = G5_OWN_IN | G5_OUT;
     a.r = s.f.p;
@@ -121,6 +124,7 @@ static int schur_residual64(const Slot& s, const void* x, void* tmp, void* out, 
     a.in = x;
     a.out = tmp;
     a.mhop = mat(s.c, M_AINV, h->Ns);
+    set_sop(a, s.c, SOP_AINV);
     a.c_hop = 1.0;
     int rc = launch_hop(h, ST_DOUBLE, 1, true, false, false, EPI_STORE, a, st);
     if (rc) return rc;
@@ -129,6 +133,7 @@ static int schur_residual64(const Slot& s, const void* x, void* tmp, void* out, 
     b.own = x;
     b.out = out;
     b.mown = mat(s.c, M_AP, h->Ns);
+    set_sop(b, s.c, SOP_A);
     b.c_hop = -0.25;
     b.x = s.ws->bh;
     b.slot = rslot;
@@ -150,7 +155,9 @@ static int prepare(Slot& s, cudaStream_t st) {
     int rc;
     if ((rc = launch_norm2(h, w.b_e, ST_DOUBLE, nullptr, 0, st, s.state, s.partials))) return rc;
     if ((rc = launch_norm2(h, w.b_o, ST_DOUBLE, nullptr, 1, st, s.state, s.partials))) return rc;
-    if ((rc = launch_smix(h, ST_DOUBLE, w.b_o, w.t64, mat(s.c, M_AINV, h->Ns), 1.0, st))) return rc;
+    if ((rc = launch_smix(h, ST_DOUBLE, w.b_o, w.t64, mat(s.c, M_AINV, h->Ns), 1.0, st, nullptr, nullptr, s.c,
+                          SOP_AINV)))
+        return rc;
     HopArgs a{};
     a.in = w.t64;
     a.own = w.b_e;
@@ -216,9 +223,11 @@ static int finish(Slot& s, cudaStream_t st) {
     a.a_own = 1.0;
     a.c_hop = 0.5;
     a.mhop = mat(s.c, M_AINV, h->Ns);
+    set_sop(a, s.c, SOP_AINV);
     if ((rc = launch_hop(h, ST_DOUBLE, 1, true, true, false, EPI_STORE, a, st))) return rc;
     HopArgs b{};
     b.mown = mat(s.c, M_AP, h->Ns);
+    set_sop(b, s.c, SOP_A);
     b.c_hop = -0.5;
     b.in = w.x_o;
     b.own = w.x_e;
