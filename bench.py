@@ -291,6 +291,136 @@ def run_reference(args):
     return 0
 
 
+# The paper's multiple-time-scale assignment (Section 3): the last (heaviest) factor of each scheme on
+# level 1 (k1 = 12 steps), the other factors on level 2 (k2 = 6); the gauge force on level 0 (k0 = 480).
+PAPER_STEPS = (480, 12, 6)
+
+
+def paper_levels(n_terms):
+    return [2] * (n_terms - 1) + [1]
+
+
+def scheme_pass(lat, binding, inputs, dims, opts, rank, timed):
+    """Per term of every mass-preconditioning scheme: heat-bath, action and force with their Krylov
+    iterations, and the CG iterations of one trajectory estimated with the paper's MTS schedule
+    (N^cg after Eq.(old_MP): the force of a level-l term is evaluated 2 k_l + 1 times)."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    schemes = [("no MP, Eq.(noMP)", binding.MP_NONE, []), ("old MP, Eq.(old_MP)", binding.MP_OLD, [0.1]),
+               ("new MP, Eq.(new_MP)", binding.MP_NEW, [0.1]), ("old MP cascade N=2, Eq.(old_MP_N)", binding.MP_OLD,
+                                                                [0.05, 0.2]),
+               ("new MP cascade N=2, Eq.(new_MP_N)", binding.MP_NEW, [0.05, 0.2])]
+    out = []
+    for name, code, mh in schemes:
+        terms = binding.mp_terms(code, MASS, mh, 1.0)
+        lv = paper_levels(len(terms))
+        rec, ncg = [], 0
+        t0 = time.perf_counter()
+        for i, t in enumerate(terms):
+            eta = torch.from_numpy(inputs.gaussian_spinor(dims, inputs.seed_for(1, 200 + 10 * rank + i))).to(dev)
+            phi, hb = lat.heatbath(t, eta, opts=opts)
+            S, st_a = lat.action(t, phi, opts=opts)
+            _, st_f = lat.force(t, phi, opts=opts)
+            k = PAPER_STEPS[lv[i]]
+            ncg += hb["iters"] + 2 * st_a["iters"] + (2 * k + 1) * st_f["iters"]
+            rec.append({"chirality": t.chirality, "m3": t.m3, "m4": t.m4, "m_den": t.m_den, "level": lv[i],
+                        "poles": hb["n_poles"], "hb_iters": hb["iters"], "action_iters": st_a["iters"],
+                        "force_iters": st_f["iters"], "action": S})
+        torch.cuda.synchronize()
+        out.append({"scheme": name, "heavy_masses": mh, "n_terms": len(terms), "seconds": time.perf_counter() - t0,
+                    "Ncg_trajectory_estimate": ncg, "terms": rec})
+    return out
+
+
+def md_step(lat, binding, inputs, dims, U, opts, opts_ref, beta, dtau, rank):
+    """Config-2 MD step on one lattice with the new-MP terms (m, mh, M) = (0.01, 0.1, 1): heat-bath,
+    action, force of every term, one momentum update with the gauge and fermion forces, one link
+    update, the actions again and Delta H; the mixed-precision action and force are compared with the
+    same solver run to a 100x tighter FP64 true residual."""
+    import numpy as np
+    import torch
+    dev = U.device
+    terms = binding.mp_terms(binding.MP_NEW, MASS, [0.1], 1.0)
+    rec = []
+    Ux = U.clone()
+    Lx, Ly, Lz, Lt = dims
+    P = torch.from_numpy(np.random.default_rng(inputs.seed_for(2, 500 + rank)).standard_normal(
+        (4, Lt, Lz, Ly, Lx, 8))).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    phis, S0 = [], 0.0
+    for i, t in enumerate(terms):
+        eta = torch.from_numpy(inputs.gaussian_spinor(dims, inputs.seed_for(2, 600 + 10 * rank + i))).to(dev)
+        th = time.perf_counter()
+        phi, hb = lat.heatbath(t, eta, opts=opts)
+        t_hb = time.perf_counter() - th
+        ta = time.perf_counter()
+        S, st_a = lat.action(t, phi, opts=opts)
+        t_a = time.perf_counter() - ta
+        tf = time.perf_counter()
+        F, st_f = lat.force(t, phi, opts=opts)
+        t_f = time.perf_counter() - tf
+        Sr, _ = lat.action(t, phi, opts=opts_ref)
+        Fr, _ = lat.force(t, phi, opts=opts_ref)
+        lat.momentum_update(P, F, dtau)
+        phis.append(phi)
+        S0 += S
+        rec.append({"chirality": t.chirality, "m3": t.m3, "m4": t.m4, "m_den": t.m_den,
+                    "heatbath_s": t_hb, "hb_iters": hb["iters"], "action_s": t_a, "action_iters": st_a["iters"],
+                    "force_s": t_f, "force_iters": st_f["iters"],
+                    "action_rel_err_vs_tight": abs(S - Sr) / abs(Sr),
+                    "force_rel_err_vs_tight": float(torch.linalg.vector_norm(F - Fr) / torch.linalg.vector_norm(Fr))})
+    K0 = lat.kinetic(P)  # momenta after the fermion kicks; the gauge kick and link update follow
+    Sg0 = lat.gauge_action(Ux, beta)
+    Fg = lat.gauge_force(Ux, beta)
+    lat.momentum_update(P, Fg, dtau)
+    K1 = lat.kinetic(P)
+    lat.link_update(Ux, P, dtau)
+    Sg1 = lat.gauge_action(Ux, beta)
+    S1 = 0.0
+    for t, phi in zip(terms, phis):
+        S1 += lat.action(t, phi, opts=opts)[0]
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    lat.set_gauge(U)
+    return {"terms": rec, "seconds": secs, "beta": beta, "dtau": dtau,
+            "dS_fermion": S1 - S0, "dS_gauge": Sg1 - Sg0, "dK_gauge_kick": K1 - K0,
+            "what": "per term heat-bath, action, force (mixed precision, true residual 1e-10; errors against the "
+                    "same solver at 1e-12), then P += dtau (F_gauge + sum F_terms), U <- exp(i dtau P) U, actions "
+                    "again"}
+
+
+def hmc_trajectory(lat, binding, inputs, dims, U, opts, beta, rank, steps=PAPER_STEPS):
+    """One HMC trajectory of length 1 with the new MP (m, mh, M) = (0.01, 0.1, 1): heat-bath of every
+    term, then the nested Omelyan integrator on the paper's (k0, k1, k2) schedule; Delta H and the
+    CG iterations of the whole trajectory."""
+    import numpy as np
+    import torch
+    dev = U.device
+    terms = binding.mp_terms(binding.MP_NEW, MASS, [0.1], 1.0)
+    Lx, Ly, Lz, Lt = dims
+    Ux = U.clone()
+    P = torch.from_numpy(np.random.default_rng(inputs.seed_for(1, 700 + rank)).standard_normal(
+        (4, Lt, Lz, Ly, Lx, 8))).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    phis, hb_iters = [], 0
+    for i, t in enumerate(terms):
+        eta = torch.from_numpy(inputs.gaussian_spinor(dims, inputs.seed_for(1, 800 + 10 * rank + i))).to(dev)
+        phi, hb = lat.heatbath(t, eta, opts=opts)
+        phis.append(phi)
+        hb_iters += hb["iters"]
+    t_hb = time.perf_counter() - t0
+    st = lat.md(Ux, P, beta, terms, phis, paper_levels(len(terms)), list(steps), tau=1.0, opts=opts)
+    torch.cuda.synchronize()
+    lat.set_gauge(U)
+    return {"dims": list(dims), "beta": beta, "steps_k0_k1_k2": list(steps),
+            "levels": paper_levels(len(terms)), "heatbath_seconds": t_hb, "heatbath_iters": hb_iters,
+            "md_seconds": st["seconds"], "seconds": time.perf_counter() - t0, "dH": st["dH"],
+            "force_evals": st["force_evals"][:3], "link_updates": st["link_updates"], "md_cg_iters": st["cg_iters"],
+            "K0": st["K0"], "K1": st["K1"], "Sg0": st["Sg0"], "Sg1": st["Sg1"], "Sf0": st["Sf0"], "Sf1": st["Sf1"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -318,6 +448,8 @@ def main():
                     help="CGNE iterations the reference arm scales one oracle iteration by: the FP64 CGNE "
                          "iteration count of this workload (1103 on the GPU, same seeded system)")
     ap.add_argument("--dims", default=None, help="override lattice, e.g. 16,16,16,16 (profiling only)")
+    ap.add_argument("--beta", type=float, default=6.2, help="Wilson plaquette coupling of the MD sections")
+    ap.add_argument("--no-hmc", action="store_true", help="skip the HMC trajectory section")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -463,28 +595,20 @@ def main():
     # ---- the rest of the hot path on the same lattice --------------------------------------------
     extra = {}
     if not args.quick:
-        from paper_1710_09621_gb300.binding import MP_NEW, Net, mp_terms
+        from paper_1710_09621_gb300 import binding as binding_mod
+        from paper_1710_09621_gb300.binding import Net
 
-        # one pass of the new-MP EOFA term list (heat-bath, action, force per term), Eq.(new_MP)
-        terms = mp_terms(MP_NEW, MASS, [0.1], 1.0)
-        eta = torch.from_numpy(inputs.gaussian_spinor(DIMS, inputs.seed_for(1, 200 + rank))).to(dev)
+        # every mass-preconditioning scheme's terms: heat-bath, action, force and N^cg (Section 2)
         hp_opts = solve_opts(tol=TOL, prec=args.prec, delta=args.delta)
-
-        def hot_pass():
-            rec = []
-            for t in terms:
-                phi, hb = lat.heatbath(t, eta, opts=hp_opts)
-                S, st_a = lat.action(t, phi, opts=hp_opts)
-                F, st_f = lat.force(t, phi, opts=hp_opts)
-                rec.append({"chirality": t.chirality, "m3": t.m3, "m4": t.m4, "m_den": t.m_den,
-                            "poles": hb["n_poles"], "hb_iters": hb["iters"], "action": S,
-                            "action_iters": st_a["iters"], "force_iters": st_f["iters"],
-                            "force_magnitude": float(torch.sqrt((F ** 2).sum()).item() / (4 * F[0].numel() / 8))})
-            return rec
-        rec, t_hp = timed(hot_pass)
-        extra["hot_path_new_mp"] = {"seconds": t_hp, "terms": rec,
-                                    "what": "heat-bath (batched pole solves) + action + force for each term of "
-                                            "(m,m)/(M,M) = (m,m)/(m,mh) (m,mh)/(M,mh) (M,mh)/(M,M), m=0.01, mh=0.1, M=1"}
+        rec, t_hp = timed(lambda: scheme_pass(lat, binding_mod, inputs, DIMS, hp_opts, rank, timed))
+        extra["schemes"] = {"seconds": t_hp, "schemes": rec,
+                            "what": "per term of (m,m)/(M,M), m=0.01, M=1: heat-bath (batched pole solves), action "
+                                    "and force; Ncg_trajectory_estimate = sum over terms of heat-bath + 2 actions + "
+                                    "(2 k + 1) forces with the paper's MTS levels (k1 = 12 for the last factor, "
+                                    "k2 = 6 for the others)"}
+        # one HMC trajectory on the paper's schedule (480, 12, 6) with the new-MP terms (Section 3)
+        if not args.no_hmc:
+            extra["hmc_trajectory"] = hmc_trajectory(lat, binding_mod, inputs, DIMS, U, hp_opts, args.beta, rank)
         # batch of 4 systems with different masses vs one after another
         m12 = [(MASS, MASS), (MASS, 0.1), (1.0, 0.1), (0.1, 0.1)]
         bsb = [torch.from_numpy(inputs.gaussian_spinor5(DIMS, NS, inputs.seed_for(1, 300 + i))).to(dev) for i in range(4)]
@@ -516,7 +640,8 @@ def main():
         l24 = ODWF(D24, NS, M0, om)
         U24 = inputs.random_su3_links(D24, EPS, inputs.seed_for(2, rank))
         plaq24 = average_plaquette(U24)
-        l24.set_gauge(torch.from_numpy(U24).to(dev))
+        U24d = torch.from_numpy(U24).to(dev)
+        l24.set_gauge(U24d)
         del U24
         b24 = torch.from_numpy(inputs.gaussian_spinor5(D24, NS, inputs.seed_for(2, 100 + rank))).to(dev)
         l24.solve(b24, MASS, MASS, opts=opts)
@@ -524,6 +649,12 @@ def main():
         (_, st24), t24 = timed(lambda: l24.solve(b24, MASS, MASS, opts=opts))
         p24 = l24.profile_read()
         l24.profile(False)
+        # config 2: one MD step with the new-MP terms on this lattice
+        extra["md_step_24"] = md_step(l24, binding_mod, inputs, D24, U24d,
+                                      solve_opts(tol=TOL, prec=args.prec, delta=args.delta),
+                                      solve_opts(tol=1e-12, prec=args.prec, delta=args.delta), args.beta,
+                                      1.0 / (2 * PAPER_STEPS[0]), rank)
+        del U24d
         Vh24 = D24[0] * D24[1] * D24[2] * D24[3] // 2
         k24 = []
         for key, (n, ms) in sorted(p24.items(), key=lambda kv: -kv[1][1]):

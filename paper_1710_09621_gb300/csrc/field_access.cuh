@@ -241,8 +241,9 @@ template <>
 __device__ __forceinline__ const SStructT<double>& sst_of<double>(const SStruct& s) { return s.d; }
 
 // Shared-memory geometry of the structured staging rows: row stride kSRow reals, site stride kSSite
-// reals (16 x 28 + 16 floats: the column loads of the 24 active lanes of a warp and the 16-byte row
-// stores are both free of bank conflicts beyond their minimum wavefront count).
+// reals. With 28-float rows the 16-byte row stores of 8 consecutive slices hit 8 distinct 4-bank
+// groups, and the column loads of one site (a half-warp: 12 lanes reading the 24 reals of one row)
+// hit 24 distinct banks.
 template <typename R>
 constexpr int kSRow = sizeof(R) == 4 ? 28 : 26;
 template <typename R>
@@ -314,24 +315,40 @@ __device__ __forceinline__ void s_a_col(const SStructT<R>& k, int c, R* xr, R* x
     }
 }
 
+// in-register reversal of the s order of one column (a per-lane select, so that every lane can load
+// and store its rows in the same order)
+template <typename R, int N>
+__device__ __forceinline__ void col_reverse(bool rev, R* x) {
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+        const R a = x[i], b = x[N - 1 - i];
+        x[i] = rev ? b : a;
+        x[N - 1 - i] = rev ? a : b;
+    }
+}
+
 // The column pass of thread j of one site (site: its staged rows, row stride rs); threads j >= 12
 // have no column. P_+ components (j < 6) run forward in s and P_- ones backward, both reversed for
-// a transposed operator.
+// a transposed operator. All lanes load and store the rows in s order (the P_+ and P_- columns of a
+// site then lie in one row, on distinct banks) and the reversed lanes flip their registers instead.
 template <typename R, int N>
 __device__ __forceinline__ void s_struct_col(const SStruct& sc, int sop, R* site, int rs, int j) {
     if (j >= 12) return;
     const SStructT<R>& k = sst_of<R>(sc);
     const int c = j < 6 ? 0 : 1;
     const bool rev = (c == 1) != ((sop & SOP_T) != 0);
-    R* p0 = site + 2 * j + (rev ? (N - 1) * rs : 0);
-    const int step = rev ? -rs : rs;
+    R* p0 = site + 2 * j;
     R xr[N], xi[N];
 #pragma unroll
-    for (int q = 0; q < N; ++q) pair_ld(p0 + q * step, xr[q], xi[q]);
+    for (int q = 0; q < N; ++q) pair_ld(p0 + q * rs, xr[q], xi[q]);
+    col_reverse<R, N>(rev, xr);
+    col_reverse<R, N>(rev, xi);
     if ((sop & 3) == SOP_AINV) s_ainv_col<R, N>(k, c, xr, xi);
     else s_a_col<R, N>(k, c, xr, xi);
+    col_reverse<R, N>(rev, xr);
+    col_reverse<R, N>(rev, xi);
 #pragma unroll
-    for (int q = 0; q < N; ++q) pair_st(p0 + q * step, xr[q], xi[q]);
+    for (int q = 0; q < N; ++q) pair_st(p0 + q * rs, xr[q], xi[q]);
 }
 
 // out = [out +] the staged row at p (24 reals, 16-byte aligned)

@@ -30,17 +30,17 @@ def lib():
     return binding
 
 
-def _setup(lib, eps=0.4, seed=41):
-    om = inputs.omega_zolotarev(NS, 0.05, 6.2)
-    U = inputs.random_su3_links(DIMS, eps, seed)
-    lat = lib.ODWF(DIMS, NS, M0, om)
+def _setup(lib, eps=0.4, seed=41, dims=DIMS, ns=NS):
+    om = inputs.omega_zolotarev(ns, 0.05, 6.2)
+    U = inputs.random_su3_links(dims, eps, seed)
+    lat = lib.ODWF(dims, ns, M0, om)
     Ud = torch.from_numpy(U).cuda()
     lat.set_gauge(Ud)
     return lat, U, Ud, om
 
 
-def _momenta(seed):
-    Lx, Ly, Lz, Lt = DIMS
+def _momenta(seed, dims=DIMS):
+    Lx, Ly, Lz, Lt = dims
     return np.random.default_rng(seed).standard_normal((4, Lt, Lz, Ly, Lx, 8))
 
 
@@ -72,10 +72,12 @@ def _terms(lib):
 
 
 def test_trajectory_matches_oracle(lib):
-    lat, U, Ud, om = _setup(lib)
-    P = _momenta(2)
+    # a smaller lattice than the other tests: the oracle integrates with numpy solves
+    dims, ns = (4, 2, 2, 4), 4
+    lat, U, Ud, om = _setup(lib, dims=dims, ns=ns)
+    P = _momenta(2, dims)
     terms, specs = _terms(lib)
-    phis = [inputs.gaussian_spinor(DIMS, 50 + i) for i in range(len(terms))]
+    phis = [inputs.gaussian_spinor(dims, 50 + i) for i in range(len(terms))]
     # the paper's assignment (Section 3): the heaviest factor on level 1, the two lighter ones on level 2
     levels, steps, tau = [2, 2, 1], [4, 2, 1], 0.25
     Pd = torch.from_numpy(P).cuda()
