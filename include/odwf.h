@@ -282,12 +282,19 @@ int eofa_solve_learned(odwf_t* h, odwf_net_t* net, double m1, double m2, const v
 int eofa_solve_gcr(odwf_t* h, odwf_net_t* net, double m1, double m2, const void* b, void* x, int nvec, int truncate,
                    const odwf_solve_opts* opts, odwf_solve_stats* stats, void* stream);
 
-/* Autotuner: times the launch choices (grid size: one resident wave, one CTA per site group, two or
+/* Autotuner: times the launch choices (tile: the default number of sites per CTA or twice it, as long
+ * as the CTA stays within 256 threads; grid size: one resident wave, one CTA per site group, two or
  * four waves; per-thread neighbour gathers or bulk-staged gathers) of the four fused kernels of the
  * CGNE iteration in precision prec on this handle's lattice and keeps the fastest for later calls.
  * report (may be NULL) receives the timings as text. Overwrites the handle's inner work fields and
- * solver state; call it between solves. */
+ * solver state; call it between solves. The paper has no counterpart (a tuning aid). */
 int odwf_autotune(odwf_t* h, int prec, char* report, int report_len, void* stream);
+
+/* Persisted autotuner choices: if the text file `path` holds an entry for this device name, lattice,
+ * Ns and precision, its choices are applied (*hit = 1, no timing); otherwise odwf_autotune runs and
+ * its choices are appended to the file as one line (*hit = 0). Returns ODWF_EINVAL if the file cannot
+ * be appended to. Entries are plain text: device|LxxLyxLzxLt|Ns|prec|key:grid-mode:staged:tile,... */
+int odwf_autotune_cache(odwf_t* h, int prec, const char* path, int* hit, void* stream);
 
 /* Kernel timing for measurement: while enabled, every launch of the library's kernels on this
  * handle (hopping, network, GCR, layout and vector kernels) is bracketed by CUDA events on its

@@ -34,7 +34,7 @@ EXPORTS = ["odwf_create", "odwf_destroy", "odwf_last_error", "odwf_set_gauge", "
            "odwf_net_num_params", "odwf_net_weights", "odwf_net_apply", "odwf_net_set_pairs", "odwf_net_loss_grad",
            "odwf_net_train", "eofa_solve_learned", "odwf_autotune", "eofa_solve_gcr", "eofa_term_spectrum",
            "hmc_gauge_action", "hmc_gauge_force", "hmc_momentum_update", "hmc_link_update", "hmc_kinetic",
-           "hmc_md"]
+           "hmc_md", "odwf_autotune_cache"]
 
 
 class OdwfError(RuntimeError):
@@ -128,6 +128,7 @@ def load_library(path: str = LIB_PATH):
     lib.eofa_mp_terms.argtypes = [i, d, dp, i, d, i, ctypes.POINTER(Term), i, ip]
     lib.odwf_apply_noalloc.argtypes = [vp, i, d, d, vp, vp, i, vp]
     lib.odwf_autotune.argtypes = [vp, i, ctypes.c_char_p, i, vp]
+    lib.odwf_autotune_cache.argtypes = [vp, i, ctypes.c_char_p, ip, vp]
     lib.odwf_net_create.argtypes = [vp, i, ctypes.POINTER(vp)]
     lib.odwf_net_destroy.argtypes = [vp]
     lib.odwf_net_num_params.argtypes = [vp]
@@ -380,6 +381,14 @@ class ODWF:
         buf = ctypes.create_string_buffer(8192)
         self._check(self.lib.odwf_autotune(self.h, _PREC[prec], buf, 8192, _stream_ptr(stream)))
         return buf.value.decode()
+
+    def autotune_cached(self, path, prec="single", stream=None):
+        """Apply the choices stored in `path` for this device, lattice and precision, or tune and append
+        them; returns True on a cache hit."""
+        hit = ctypes.c_int(0)
+        self._check(self.lib.odwf_autotune_cache(self.h, _PREC[prec], str(path).encode(), ctypes.byref(hit),
+                                                 _stream_ptr(stream)))
+        return bool(hit.value)
 
     def profile(self, enable=True):
         self._check(self.lib.odwf_profile_enable(self.h, 1 if enable else 0))

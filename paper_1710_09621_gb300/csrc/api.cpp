@@ -694,13 +694,96 @@ extern "C" int odwf_autotune(odwf_t* h, int prec, char* report, int report_len, 
         std::string all;
         for (auto& l : log) all += l + "\n";
         for (auto& kv : h->tune) {
-            char buf[96];
-            std::snprintf(buf, sizeof buf, "chosen key %d: grid-mode %d staged %d\n", kv.first, kv.second.first,
-                          kv.second.second);
+            char buf[128];
+            std::snprintf(buf, sizeof buf, "chosen key %d: grid-mode %d staged %d tile x%d\n", kv.first, kv.second.mode,
+                          kv.second.staged, kv.second.spbm);
             all += buf;
         }
         std::strncpy(report, all.c_str(), report_len - 1);
         report[report_len - 1] = 0;
     }
     return rc;
+}
+
+// ---- persisted autotuner choices ---------------------------------------------------------------
+// One text line per (device, lattice, Ns, precision):
+//   <device name>|<Lx>x<Ly>x<Lz>x<Lt>|<Ns>|<prec>|<kernel key>:<grid mode>:<staged>:<tile>,...
+namespace {
+
+std::string tune_key(const odwf_s* h, int prec) {
+    int dev = 0;
+    cudaDeviceProp prop{};
+    std::string name = "unknown";
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
+    for (char& ch : name)
+        if (ch == '|' || ch == '\n') ch = '_';
+    char buf[256];
+    std::snprintf(buf, sizeof buf, "%s|%dx%dx%dx%d|%d|%d", name.c_str(), h->L[0], h->L[1], h->L[2], h->L[3], h->Ns,
+                  prec);
+    return buf;
+}
+
+int tune_storage_of(int prec) { return prec == ODWF_PREC_DOUBLE ? ST_DOUBLE : (prec == ODWF_PREC_SINGLE ? ST_FLOAT : ST_HALF); }
+
+}  // namespace
+
+extern "C" int odwf_autotune_cache(odwf_t* h, int prec, const char* path, int* hit, void* stream) {
+    if (!h || !path || !hit) return set_err(h, ODWF_EINVAL, "null argument");
+    if (prec != ODWF_PREC_DOUBLE && prec != ODWF_PREC_SINGLE && prec != ODWF_PREC_HALF)
+        return set_err(h, ODWF_EINVAL, "autotune: bad precision");
+    *hit = 0;
+    const std::string key = tune_key(h, prec);
+    const int stg = tune_storage_of(prec);
+    if (FILE* f = std::fopen(path, "r")) {
+        char line[4096];
+        std::string found;
+        while (std::fgets(line, sizeof line, f)) {
+            std::string l(line);
+            while (!l.empty() && (l.back() == '\n' || l.back() == '\r')) l.pop_back();
+            if (l.size() > key.size() && l.compare(0, key.size(), key) == 0 && l[key.size()] == '|')
+                found = l.substr(key.size() + 1);  // the last entry for the key wins
+        }
+        std::fclose(f);
+        if (!found.empty()) {
+            std::map<int, TuneChoice> parsed;
+            size_t pos = 0;
+            bool bad = false;
+            while (pos < found.size()) {
+                size_t end = found.find(',', pos);
+                if (end == std::string::npos) end = found.size();
+                int k = 0;
+                TuneChoice tc;
+                if (std::sscanf(found.substr(pos, end - pos).c_str(), "%d:%d:%d:%d", &k, &tc.mode, &tc.staged, &tc.spbm) != 4 ||
+                    tc.mode < 0 || tc.mode > 3 || tc.staged < 0 || tc.staged > 1 || tc.spbm < 1 || tc.spbm > 2 ||
+                    (k / 100000) % 10 != stg) {
+                    bad = true;
+                    break;
+                }
+                parsed[k] = tc;
+                pos = end + 1;
+            }
+            if (!bad && !parsed.empty()) {
+                for (auto& kv : parsed) h->tune[kv.first] = kv.second;
+                *hit = 1;
+                return ODWF_OK;
+            }
+        }
+    }
+    int rc = odwf_autotune(h, prec, nullptr, 0, stream);
+    if (rc) return rc;
+    std::string entry = key + "|";
+    bool first = true;
+    for (auto& kv : h->tune) {
+        if ((kv.first / 100000) % 10 != stg) continue;
+        char buf[64];
+        std::snprintf(buf, sizeof buf, "%s%d:%d:%d:%d", first ? "" : ",", kv.first, kv.second.mode, kv.second.staged,
+                      kv.second.spbm);
+        entry += buf;
+        first = false;
+    }
+    FILE* f = std::fopen(path, "a");
+    if (!f) return set_err(h, ODWF_EINVAL, std::string("cannot append to the autotuner cache ") + path);
+    std::fprintf(f, "%s\n", entry.c_str());
+    std::fclose(f);
+    return ODWF_OK;
 }

@@ -863,9 +863,10 @@ struct KernelPick {
 };
 
 template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
-static int occupancy(odwf_s* h, int kind, size_t* smem_out) {
+static int occupancy(odwf_s* h, int kind, size_t* smem_out, int spb = 0) {
     using R = typename Store<ST>::R;
-    const int Ns = h->Ns, spb = spb_for(Ns);
+    const int Ns = h->Ns;
+    if (spb <= 0) spb = spb_for(Ns);
     size_t smem = sizeof(R) * ((size_t)(MIXHOP + MIXOWN) * 2 * Ns * Ns + (size_t)spb * Ns * kRowStride<R>);
     // A-fragment tables of the tensor-core s-mixing (FP32 arithmetic, Ns = 16)
     if (std::is_same<R, float>::value && Ns == 16 && !kLeanHop<ST, HOP, MIXHOP, OWN, MIXOWN>)
@@ -875,7 +876,7 @@ static int occupancy(odwf_s* h, int kind, size_t* smem_out) {
     }
     if (kind == 4) smem = sizeof(R) * (size_t)spb * kSSite<R>;
     *smem_out = smem;
-    static int occ_cache[5][kMaxNs + 1] = {{0}};
+    static std::map<long, int> occ_cache;  // (kind, Ns, sites per CTA) -> resident CTAs per SM
     static bool attr_set[5][2] = {{false, false}, {false, false}, {false, false}, {false, false}, {false, false}};
     const bool ws = warp_sites(Ns);
     const void* fn = KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::fn(kind, ws);
@@ -883,7 +884,7 @@ static int occupancy(odwf_s* h, int kind, size_t* smem_out) {
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set[kind][ws] = true;
     }
-    int& occ = occ_cache[kind][Ns];
+    int& occ = occ_cache[((long)kind * 64 + Ns) * 1024 + spb];
     if (occ == 0) {
         int o = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, Ns * spb, smem) != cudaSuccess || o < 1) o = 1;
@@ -923,20 +924,23 @@ static int launch_multi_one(odwf_s* h, const HopArgs* dev_args, int n, int max_v
 
 template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
 static int launch_one(odwf_s* h, int parity, HopArgs a, cudaStream_t st) {
-    const int Ns = h->Ns, spb = spb_for(Ns);
+    const int Ns = h->Ns;
+    int spb = spb_for(Ns);
     size_t smem = 0;
     const int base_key = ST * 100000 + HOP * 10000 + MIXHOP * 1000 + OWN * 100 + MIXOWN * 10 + EPI;
     bool stg = KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::CAN_STAGE && staged_ok(h, ST);
     int mode = 0;
     auto tuned = h->tune.find(base_key);
     if (tuned != h->tune.end()) {
-        mode = tuned->second.first;
-        stg = KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::CAN_STAGE && staged_geom_ok(h, ST) && tuned->second.second;
+        mode = tuned->second.mode;
+        stg = KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::CAN_STAGE && staged_geom_ok(h, ST) && tuned->second.staged;
+        // tile: a multiple of the default sites per CTA while the CTA stays within 256 threads
+        if (tuned->second.spbm > 1 && spb * tuned->second.spbm * Ns <= 256) spb *= tuned->second.spbm;
     }
     // the structured fifth-dimension product: single-system per-thread-gather kernels at Ns = kStructNs
     const bool sn = KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::CAN_STRUCT && !stg && Ns == kStructNs &&
                     a.sop != SOP_DENSE;
-    const int occ = occupancy<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(h, stg ? 2 : (sn ? 4 : 0), &smem);
+    const int occ = occupancy<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(h, stg ? 2 : (sn ? 4 : 0), &smem, spb);
     const int groups = (h->Vh + spb - 1) / spb;
     const int grid = grid_for_mode(h, mode, occ, groups, EPI != EPI_STORE);
     hop_fill(h, ST, parity, a, EPI != EPI_STORE);
@@ -1390,10 +1394,16 @@ int autotune_storage(odwf_s* h, int stg, const SCoef* c, cudaStream_t st, std::v
         }
         a.state = (v.epi == EPI_STORE) ? nullptr : h->state;
         float best = 1e30f;
-        std::pair<int, int> best_choice{0, 0};
+        TuneChoice best_choice{};
+        const int max_spbm = spb_for(h->Ns) * 2 * h->Ns <= 256 ? 2 : 1;
+        for (int spbm = 1; spbm <= max_spbm; ++spbm)
         for (int staged = 0; staged <= (can_stage ? 1 : 0); ++staged)
             for (int mode = 0; mode < 4; ++mode) {
-                h->tune[base_key] = {mode, staged};
+                TuneChoice tc;
+                tc.mode = mode;
+                tc.staged = staged;
+                tc.spbm = spbm;
+                h->tune[base_key] = tc;
                 int rc = fill();
                 if (rc) return set_err(h, rc, "autotune: fill");
                 for (int k = 0; k < 2; ++k)
@@ -1408,12 +1418,12 @@ int autotune_storage(odwf_s* h, int stg, const SCoef* c, cudaStream_t st, std::v
                 cudaEventElapsedTime(&ms, e0, e1);
                 ms /= reps;
                 char buf[160];
-                std::snprintf(buf, sizeof buf, "%s storage %d staged %d grid-mode %d: %.1f us", v.name, stg, staged, mode,
-                              1e3 * ms);
+                std::snprintf(buf, sizeof buf, "%s storage %d tile x%d staged %d grid-mode %d: %.1f us", v.name, stg, spbm,
+                              staged, mode, 1e3 * ms);
                 log.push_back(buf);
                 if (ms < best) {
                     best = ms;
-                    best_choice = {mode, staged};
+                    best_choice = tc;
                 }
             }
         h->tune[base_key] = best_choice;

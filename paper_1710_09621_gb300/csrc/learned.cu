@@ -15,11 +15,13 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "field_access.cuh"
+#include "tcgen05.cuh"
 
 namespace odwf {
 
@@ -37,6 +39,7 @@ constexpr int kXStride = 24;      // bf16 per A-operand row in shared memory (16
 // exactly the A-operand row the second layer feeds to the tensor cores (it rounds its inputs to BF16
 // there anyway, so the result is bit-identical to FP32 intermediates at half the bytes).
 struct NetLayerArgs {
+    unsigned int* fault;     // set to 1 if a bounded wait for the tensor cores ran out (never expected)
     const float* in[kMaxC];  // input channels (FP32 chunk layout, or BF16 rows), opposite parity
     int cin, cout;
     const float* B;          // B operand, FP32 [cin*4 k-tiles][16][8*cout]
@@ -276,6 +279,194 @@ __global__ void __launch_bounds__(256) k_net_layer(NetLayerArgs a) {
     }
 }
 
+// ---- 1 -> C layer on the fifth-generation tensor cores (tcgen05, Ns = 16) ------------------------
+// The same layer as k_net_layer<1, 2, OUTB> for CTAs of 8 sites x 16 slices = 128 threads: the channel
+// mixing of every (site, s, colour) row is D = A B with A the row of transported inputs (K = 64: 8
+// directions x 4 spins x re/im, BF16) and B the weight block (K x N, N = 16: 2 output channels x 4
+// spins x re/im). Per colour the 128 rows of the CTA are one M = 128 tile: the A rows go to shared
+// memory in the canonical K-major layout (core matrices of 8 rows x 8 BF16; one K chunk per
+// direction), B is converted once per CTA, one thread issues 3 colours x 4 K-steps of tcgen05.mma
+// (K = 16 each) into FP32 accumulators in tensor memory, and after the commit every thread reads its
+// own row of D (its own (site, s) outputs of all channels) with tcgen05.ld. No fragment loads and no
+// shared-memory staging of the results.
+constexpr int kTcRows = 128;                      // M: threads of the CTA
+constexpr int kTcK = 64;                          // K of the 1 -> C layer
+constexpr int kTcN = 16;                          // N = 8 C_out, C_out = 2
+constexpr int kTcABytes = kTcRows * kTcK * 2;     // one colour's A tile (16 KB)
+constexpr int kTcBBytes = kTcN * kTcK * 2;        // B (2 KB)
+constexpr uint32_t kTcCols = 64;                  // tensor-memory columns: D of 3 colours x 16
+
+__host__ __device__ constexpr size_t layer12_tc_smem() {
+    return (size_t)3 * kTcABytes + kTcBBytes + sizeof(uint32_t) * kAfrag16Words + 64;
+}
+
+template <bool OUTB>
+__global__ void __launch_bounds__(128) k_net_layer12_tc(NetLayerArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_tc[];
+    constexpr int Ns = 16;
+    const int s = threadIdx.x, ls = threadIdx.y, spb = blockDim.y;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+    const int lane = tid & 31, warp = tid >> 5;
+    unsigned char* Asm = smem_tc;                                         // 3 colour tiles
+    unsigned char* Bsm = smem_tc + 3 * kTcABytes;                         // N x K, K-major
+    uint32_t* afr = reinterpret_cast<uint32_t*>(Bsm + kTcBBytes);         // s-mixing fragment table
+    uint64_t* bar = reinterpret_cast<uint64_t*>(afr + kAfrag16Words);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+    volatile int* ok_s = reinterpret_cast<volatile int*>(tslot + 1);
+    float* sh = reinterpret_cast<float*>(Asm);                           // s-mixing rows, after the MMAs
+
+    // B (FP32 [4 k-tiles][16][16], K index kt 16 + kk) -> BF16 [n][k] in core matrices (k/8, n/8)
+    for (int i = tid; i < kTcN * kTcK; i += nth) {
+        const int n = i % kTcN, k = i / kTcN;
+        const float v = __ldg(a.B + (size_t)(k >> 4) * 16 * kTcN + (k & 15) * kTcN + n);
+        __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(Bsm + ((k >> 3) * 2 + (n >> 3)) * 128 + (n & 7) * 16) + (k & 7);
+        *dst = __float2bfloat16_rn(v);
+    }
+    if (a.mix) s_mix16_afrag(a.mix, afr, tid, nth);
+    if (tid == 0) tc_mbar_init(bar, 1);
+    if (warp == 0) {
+        tmem_alloc(tslot, kTcCols);
+        tmem_relinquish();
+    }
+    float w0[32];
+    if (a.w0)
+#pragma unroll
+        for (int k = 0; k < 32; ++k) w0[k] = a.w0[k];
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    constexpr uint32_t idesc = idesc_bf16_f32(kTcRows, kTcN);
+    uint32_t phase = 0;
+    bool ok = true;
+
+    for (int g = blockIdx.x; g * spb < a.Vh; g += gridDim.x) {
+        tc_fence_before();
+        __syncthreads();  // the previous group's accumulator reads and s-mixing rows are done
+        const int cb = g * spb + ls;
+        const bool valid = cb < a.Vh;
+        // A rows: per direction d one 16-byte K chunk (re spins 0..3, im spins 0..3) per colour
+#pragma unroll 1
+        for (int d = 0; d < 8; ++d) {
+            float x[24];
+            if (valid) transport4(a.in[0], a.links, a.nbr, cb, s, Ns, d, x);
+            else
+#pragma unroll
+                for (int k = 0; k < 24; ++k) x[k] = 0.f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                uint4 v;
+                v.x = pack_bf16(x[(0 * 3 + c) * 2], x[(1 * 3 + c) * 2]);
+                v.y = pack_bf16(x[(2 * 3 + c) * 2], x[(3 * 3 + c) * 2]);
+                v.z = pack_bf16(x[(0 * 3 + c) * 2 + 1], x[(1 * 3 + c) * 2 + 1]);
+                v.w = pack_bf16(x[(2 * 3 + c) * 2 + 1], x[(3 * 3 + c) * 2 + 1]);
+                *reinterpret_cast<uint4*>(Asm + c * kTcABytes + (d * 16 + (tid >> 3)) * 128 + (tid & 7) * 16) = v;
+            }
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int k = 0; k < kTcK / 16; ++k)
+                    umma_bf16(tmem + c * kTcN, smem_desc(Asm + c * kTcABytes + k * 2 * 16 * 128, 16 * 128, 128),
+                              smem_desc(Bsm + k * 2 * 2 * 128, 2 * 128, 128), idesc, k > 0 ? 1u : 0u);
+            umma_commit(bar);
+        }
+        // one thread waits (bounded) and the CTA follows its verdict, so that the warp-collective
+        // accumulator loads below run in every warp or in none
+        if (tid == 0) {
+            const bool done = tc_mbar_wait_bounded(bar, phase);
+            if (!done && a.fault) atomicOr(a.fault, 1u);
+            *ok_s = done ? 1 : 0;
+        }
+        __syncthreads();
+        if (!*ok_s) {
+            ok = false;
+            break;
+        }
+        phase ^= 1u;
+        tc_fence_after();
+        float dv[3][16];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c * kTcN, dv[c]);
+
+        float ow[24];
+        if (a.own && valid) Store<ST_FLOAT>::load(a.own, nullptr, (size_t)cb, s, Ns, ow);
+        else
+#pragma unroll
+            for (int k = 0; k < 24; ++k) ow[k] = 0.f;
+        float wown[24];  // W0 own
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                float re = 0.f, im = 0.f;
+                if (a.w0) {
+#pragma unroll
+                    for (int aa = 0; aa < 4; ++aa) {
+                        const float wr = w0[(b * 4 + aa) * 2], wi = w0[(b * 4 + aa) * 2 + 1];
+                        const float xr = ow[(aa * 3 + c) * 2], xi = ow[(aa * 3 + c) * 2 + 1];
+                        re = fmaf(wr, xr, fmaf(-wi, xi, re));
+                        im = fmaf(wr, xi, fmaf(wi, xr, im));
+                    }
+                }
+                wown[(b * 3 + c) * 2] = re;
+                wown[(b * 3 + c) * 2 + 1] = im;
+            }
+#pragma unroll
+        for (int co = 0; co < 2; ++co) {
+            float v[24];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    v[(b * 3 + c) * 2] = a.c_hop * dv[c][co * 8 + b];
+                    v[(b * 3 + c) * 2 + 1] = a.c_hop * dv[c][co * 8 + 4 + b];
+                }
+            if (a.own_in_mix)
+#pragma unroll
+                for (int k = 0; k < 24; ++k) v[k] += wown[k];
+            if (a.mix) {
+                __syncwarp();  // the warp's rows of sh are free (previous channel read)
+                row24_store(sh + (size_t)tid * 24, v);
+                __syncwarp();
+                s_mix16_tc(afr, sh, lane, warp, tid, v, false);
+            }
+            if (!a.own_in_mix && co == 0)
+#pragma unroll
+                for (int k = 0; k < 24; ++k) v[k] += wown[k];
+            if (valid) {
+                if constexpr (OUTB) {
+                    uint4* o = reinterpret_cast<uint4*>(a.out[co]) + (size_t)cb * 3 * Ns + s;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        uint4 q;
+                        q.x = pack_bf16(v[(0 * 3 + c) * 2], v[(1 * 3 + c) * 2]);
+                        q.y = pack_bf16(v[(2 * 3 + c) * 2], v[(3 * 3 + c) * 2]);
+                        q.z = pack_bf16(v[(0 * 3 + c) * 2 + 1], v[(1 * 3 + c) * 2 + 1]);
+                        q.w = pack_bf16(v[(2 * 3 + c) * 2 + 1], v[(3 * 3 + c) * 2 + 1]);
+                        o[(size_t)c * Ns] = q;
+                    }
+                } else {
+                    Store<ST_FLOAT>::store(a.out[co], nullptr, (size_t)cb, s, Ns, v);
+                }
+            }
+        }
+    }
+    if (!ok && tid == 0) {
+        // the accumulators' MMAs did not report completion within the limit: give them a last bounded
+        // wait before the tensor memory is released
+        tc_mbar_wait_bounded(bar, phase);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kTcCols);
+}
+
 // Second layer (2 input channels, 1 output) with the channel mixing BEFORE the transport. Spin
 // weights and colour transport act on different indices, so W[c,d] T_d v_c = T_d (W[c,d] v_c) with
 // both applied at the neighbour: per direction d the gathered v_0(x+d), v_1(x+d) form one K = 16
@@ -390,11 +581,12 @@ __global__ void __launch_bounds__(256) k_net_layer_mt(NetLayerArgs a) {
                     for (int q = 0; q < 4; ++q) ph[c][q] = 0.f;
                     mma_bf16(ph[c], af, bfrag[d]);
                 }
-                // U_d of each served thread's site applied to (phi colours 0..2) of spin tig
+                // U_d of each served thread's site applied to (phi colours 0..2) of spin tig; the two
+                // threads a lane serves in half h share their site when Ns >= 16 (one link load)
+                float u[20];
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
-                    float u[20];
-                    {
+                    if (e == 0 || lsite[h][1] != lsite[h][0]) {
                         const float4* lp = reinterpret_cast<const float4*>(lk) + (lsite[h][e] * 8 + d) * 5;
 #pragma unroll
                         for (int q = 0; q < 5; ++q) row4_load(reinterpret_cast<const float*>(lp + q), u + 4 * q);
@@ -684,6 +876,7 @@ struct odwf_net_s {
     float *B0 = nullptr, *B1 = nullptr, *B2 = nullptr, *B3 = nullptr, *w0f = nullptr, *w0adj = nullptr;
     bool prepped = false;
     double cm1 = -1, cm2 = -1;
+    bool no_tc = false;      // ODWF_NO_TCGEN05=1: mma.sync layers only
     double* mats = nullptr;  // transposed A^{-1} (2 Ns^2) then A^{-T} (2 Ns^2), FP64
     SCoef sc{};              // structured form of the same (for the s-mixing kernel; sc.dev unused)
     // FP32 half fields: u (even), v[C] (odd), t (even), gy (even), gh[C] (odd), delta (even)
@@ -791,6 +984,26 @@ int net_layer(odwf_net_s* n, int parity, int cin, int cout, const float* const* 
         if (h->prof) prof_end(h, key, st, ev0);
         return cuda_check(h, cudaGetLastError(), "k_net_layer");
     };
+    if (cin == 1 && cout == 2 && h->Ns == 16 && spb == 8 && !n->no_tc) {
+        // the tcgen05 layer: its own shared-memory layout and a bounded wait (read by check_fault)
+        a.fault = h->fault;
+        h->staged_used = true;
+        auto fn = bf16 ? k_net_layer12_tc<true> : k_net_layer12_tc<false>;
+        static bool set_tc[2] = {false, false};
+        const size_t smem_tc = layer12_tc_smem();
+        if (!set_tc[bf16 ? 1 : 0]) {
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tc);
+            set_tc[bf16 ? 1 : 0] = true;
+        }
+        int occ = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, h->Ns * spb, smem_tc);
+        const int key = 2000000 + (bf16 ? 1000 : 0) + cin * 100 + cout * 10 + (own ? 1 : 0);
+        cudaEvent_t ev0 = nullptr;
+        if (h->prof) prof_begin(h, key, st, &ev0);
+        fn<<<grid_for_groups(h, occ < 1 ? 1 : occ), blk, smem_tc, st>>>(a);
+        if (h->prof) prof_end(h, key, st, ev0);
+        return cuda_check(h, cudaGetLastError(), "k_net_layer12_tc");
+    }
     if (cin == 1 && cout == 2) return bf16 ? launch(k_net_layer<1, 2, true>, 0) : launch(k_net_layer<1, 2, false>, 1);
     if (cin == 2 && cout == 1) return bf16 ? launch(k_net_layer_mt<true>, 2) : launch(k_net_layer_mt<false>, 3);
     if (cin == 1 && cout == 1) return launch(k_net_layer<1, 1, false>, 4);
@@ -942,6 +1155,7 @@ extern "C" int odwf_net_create(odwf_t* h, int channels, odwf_net_t** out) {
     odwf_net_s* n = new odwf_net_s();
     n->h = h;
     n->C = channels;
+    if (const char* e = std::getenv("ODWF_NO_TCGEN05")) n->no_tc = (e[0] == '1');
     n->P = 16 + 2 * channels * 8 * 16;
     const int C = channels;
     int rc = ODWF_OK;

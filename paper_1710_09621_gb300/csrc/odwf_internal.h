@@ -120,6 +120,14 @@ struct HopArgs {
 };
 
 // ---- host-side handle --------------------------------------------------------------------------
+// Launch choice of a fused hop kernel: grid mode (0 one resident wave, 1 one CTA per site group, 2 / 3
+// two / four waves), bulk-staged gathers or not, and the tile: spbm x the default sites per CTA.
+struct TuneChoice {
+    int mode = 0;
+    int staged = 0;
+    int spbm = 1;
+};
+
 struct SCoef {
     // kNumCoef transposed Ns x Ns matrices, in this order:
     //  0 A_+(m1), 1 A_-(m2), 2 A_+^{-1}, 3 A_-^{-1}, 4 A_+^T, 5 A_-^T, 6 A_+^{-T}, 7 A_-^{-T},
@@ -175,8 +183,8 @@ struct odwf_s {
     long long wait_cycles = 0;            // HopArgs::wait_cycles (ODWF_TEST_WAIT_CYCLES, tests only)
     int staged = 0;                       // use the bulk-staged hop kernels where they apply (ODWF_STAGED=1)
     bool dense_s = false;                 // dense Ns x Ns fifth-dimension products everywhere (ODWF_DENSE_S=1)
-    // autotuned launch choice per kernel variant (key without the staged flag): grid mode, staged
-    std::map<int, std::pair<int, int>> tune;
+    // autotuned launch choice per kernel variant (key without the staged flag)
+    std::map<int, odwf::TuneChoice> tune;
     // batch-solve pools: per-system workspaces, solver states, reduction buffers, kernel arguments
     std::vector<odwf::Workspace> bws;
     odwf::CGState* bstate = nullptr;

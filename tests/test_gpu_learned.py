@@ -157,3 +157,43 @@ def test_gcr_rejects_bad_basis_and_reports_noconv(env):
     _, st = lat.solve_gcr(b, M1, M2, nvec=4, opts=binding.solve_opts(tol=1e-10, prec="single", maxiter=3),
                           allow_noconv=True)
     assert st["status"] == binding.ODWF_ENOCONV and st["iters"] == 3 and st["true_residual"] > 1e-10
+
+
+@pytest.mark.parametrize("no_tc", ["0", "1"])
+def test_net_ns16_tensor_memory_layer(no_tc, monkeypatch):
+    """At Ns = 16 the 1 -> 2 layer (forward, and the first adjoint layer) runs on the fifth-generation
+    tensor cores: tcgen05.mma with FP32 accumulators in tensor memory; ODWF_NO_TCGEN05=1 selects the
+    mma.sync layer. Both against the oracle (BF16 tolerance 2e-2 outputs, 5e-2 weight gradients), and the
+    preconditioned solve meets the FP64 true residual."""
+    monkeypatch.setenv("ODWF_NO_TCGEN05", no_tc)
+    from paper_1710_09621_gb300 import build
+    build.build()
+    from paper_1710_09621_gb300 import binding
+    dims, Ns = (4, 4, 4, 8), 16
+    om = inputs.omega_zolotarev(Ns, 0.05, 6.2)
+    U = inputs.random_su3_links(dims, 0.4, 73)
+    lat = binding.ODWF(dims, Ns, 1.3, om)
+    lat.set_gauge(torch.from_numpy(U).cuda())
+    op = OracleODWF(U, 1.3, om)
+    sch = solver.Schur(op, M1, M2)
+    net = binding.Net(lat, 2)
+    W = _rand_weights(2, 11)
+    net.set_weights(W.flat())
+    M = learned.LearnedPreconditioner(sch, W)
+    r = inputs.gaussian_spinor5(dims, Ns, 12)
+    assert _rel(net.apply(torch.from_numpy(r).cuda(), M1, M2).cpu().numpy(), M.forward(r * sch.even)) < 2e-2
+    assert _rel(net.apply(torch.from_numpy(r).cuda(), M1, M2, adjoint=True).cpu().numpy(),
+                M.adjoint(r * sch.even)) < 2e-2
+    rs = [inputs.gaussian_spinor5(dims, Ns, 13 + i) for i in range(2)]
+    es = [inputs.gaussian_spinor5(dims, Ns, 23 + i) for i in range(2)]
+    net.set_pairs([torch.from_numpy(x).cuda() for x in rs], M1, M2, es=[torch.from_numpy(x).cuda() for x in es])
+    L, g = net.loss_grad()
+    Lo, Go = M.loss_and_grad([x * sch.even for x in rs], [x * sch.even for x in es])
+    assert abs(L - Lo) < 2e-2 * Lo and _rel(g, Go.flat()) < 5e-2
+    neu = binding.Net(lat, 2)
+    b = inputs.gaussian_spinor5(dims, Ns, 33)
+    x, st = neu.solve(torch.from_numpy(b).cuda(), M1, M2, opts=binding.solve_opts(tol=1e-10, prec="single", delta=1e-3))
+    assert np.linalg.norm(b - op.ht(x.cpu().numpy(), M1, M2)) / np.linalg.norm(b) <= 1.05e-10
+    net.close()
+    neu.close()
+    lat.close()

@@ -215,3 +215,31 @@ def test_dense_fifth_dimension_fallback(lib, prec, monkeypatch):
         res = np.linalg.norm(b - op.ht(x.cpu().numpy(), 0.01, 0.3)) / np.linalg.norm(b)
         assert res <= 1.05e-10, (dense, res)
         lat.close()
+
+
+def test_autotune_cache_persists_and_tiles(lib, tmp_path):
+    """odwf_autotune_cache: the first handle tunes and appends its choices, a second handle of the same
+    lattice loads them without timing; a hand-written entry that asks for the doubled tile (twice the
+    default sites per CTA) on every fused kernel, with and without bulk staging, still agrees with the oracle."""
+    case = CASES[2]
+    path = tmp_path / "tune.txt"
+    lat, op = _setup(lib, *case)
+    assert lat.autotune_cached(path, "single") is False
+    assert "8x8x8x16|16|1|" in path.read_text()
+    lat.close()
+    lat2, op2 = _setup(lib, *case)
+    assert lat2.autotune_cached(path, "single") is True
+    _apply_checks(lat2, op2, case, (0.05, 0.5), "single")
+    lat2.close()
+    name = torch.cuda.get_device_name()
+    for staged in (0, 1):
+        forced = tmp_path / f"forced{staged}.txt"
+        keys = [111000, 110112, 110113, 110110]   # K1, CGNE forward / adjoint halves, D_T parity block (FP32)
+        forced.write_text(f"{name}|8x8x8x16|16|1|" + ",".join(f"{k}:{staged * 2}:{staged}:2" for k in keys) + "\n")
+        lat3, op3 = _setup(lib, *case)
+        assert lat3.autotune_cached(forced, "single") is True
+        _apply_checks(lat3, op3, case, (0.05, 0.5), "single")
+        b = inputs.gaussian_spinor5(case[0], case[1], 270)
+        x, st = lat3.solve(torch.from_numpy(b).cuda(), 0.05, 0.1, opts=lib.solve_opts(tol=1e-10, prec="single"))
+        assert np.linalg.norm(b - op3.ht(x.cpu().numpy(), 0.05, 0.1)) / np.linalg.norm(b) <= 1.05e-10
+        lat3.close()
