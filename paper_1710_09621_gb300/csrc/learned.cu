@@ -284,8 +284,11 @@ __global__ void __launch_bounds__(256) k_net_layer(NetLayerArgs a) {
 // mixing of every (site, s, colour) row is D = A B with A the row of transported inputs (K = 64: 8
 // directions x 4 spins x re/im, BF16) and B the weight block (K x N, N = 16: 2 output channels x 4
 // spins x re/im). Per colour the 128 rows of the CTA are one M = 128 tile: the A rows go to shared
-// memory in the canonical K-major layout (core matrices of 8 rows x 8 BF16; one K chunk per
-// direction), B is converted once per CTA, one thread issues 3 colours x 4 K-steps of tcgen05.mma
+// memory in the canonical K-major layout (core matrices of 8 rows x 8 BF16, one K chunk per
+// direction; the 8 K chunks of an 8-row group are contiguous, 1024 bytes per group, so the
+// descriptor strides are 128 bytes along K and 1024 along M and every K-step of 16 reads inside its
+// tile), B likewise (2 groups of 8 columns), converted once per CTA; one thread issues 3 colours x 4
+// K-steps of tcgen05.mma
 // (K = 16 each) into FP32 accumulators in tensor memory, and after the commit every thread reads its
 // own row of D (its own (site, s) outputs of all channels) with tcgen05.ld. No fragment loads and no
 // shared-memory staging of the results.
@@ -319,7 +322,7 @@ __global__ void __launch_bounds__(128) k_net_layer12_tc(NetLayerArgs a) {
     for (int i = tid; i < kTcN * kTcK; i += nth) {
         const int n = i % kTcN, k = i / kTcN;
         const float v = __ldg(a.B + (size_t)(k >> 4) * 16 * kTcN + (k & 15) * kTcN + n);
-        __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(Bsm + ((k >> 3) * 2 + (n >> 3)) * 128 + (n & 7) * 16) + (k & 7);
+        __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(Bsm + (n >> 3) * 1024 + (k >> 3) * 128 + (n & 7) * 16) + (k & 7);
         *dst = __float2bfloat16_rn(v);
     }
     if (a.mix) s_mix16_afrag(a.mix, afr, tid, nth);
@@ -361,7 +364,7 @@ __global__ void __launch_bounds__(128) k_net_layer12_tc(NetLayerArgs a) {
                 v.y = pack_bf16(x[(2 * 3 + c) * 2], x[(3 * 3 + c) * 2]);
                 v.z = pack_bf16(x[(0 * 3 + c) * 2 + 1], x[(1 * 3 + c) * 2 + 1]);
                 v.w = pack_bf16(x[(2 * 3 + c) * 2 + 1], x[(3 * 3 + c) * 2 + 1]);
-                *reinterpret_cast<uint4*>(Asm + c * kTcABytes + (d * 16 + (tid >> 3)) * 128 + (tid & 7) * 16) = v;
+                *reinterpret_cast<uint4*>(Asm + c * kTcABytes + (tid >> 3) * 1024 + d * 128 + (tid & 7) * 16) = v;
             }
         }
         fence_proxy_async_smem();
@@ -372,8 +375,8 @@ __global__ void __launch_bounds__(128) k_net_layer12_tc(NetLayerArgs a) {
             for (int c = 0; c < 3; ++c)
 #pragma unroll
                 for (int k = 0; k < kTcK / 16; ++k)
-                    umma_bf16(tmem + c * kTcN, smem_desc(Asm + c * kTcABytes + k * 2 * 16 * 128, 16 * 128, 128),
-                              smem_desc(Bsm + k * 2 * 2 * 128, 2 * 128, 128), idesc, k > 0 ? 1u : 0u);
+                    umma_bf16(tmem + c * kTcN, smem_desc(Asm + c * kTcABytes + k * 2 * 128, 128, 1024),
+                              smem_desc(Bsm + k * 2 * 128, 128, 1024), idesc, k > 0 ? 1u : 0u);
             umma_commit(bar);
         }
         // one thread waits (bounded) and the CTA follows its verdict, so that the warp-collective
