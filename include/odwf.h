@@ -258,7 +258,13 @@ int odwf_net_apply(odwf_net_t* net, double m1, double m2, const void* r, void* o
  * library solves for e_i itself (FP32 CGNE with FP64 reliable updates to tol). */
 int odwf_net_set_pairs(odwf_net_t* net, double m1, double m2, int npairs, const void* const* r,
                        const void* const* e, double tol, void* stream);
-/* L = sum_i |M r_i - e_i|^2 / |e_i|^2 and dL/dconj(W) (host complex128, may be NULL). */
+/* Training loss of odwf_net_loss_grad / odwf_net_train: ODWF_NET_LOSS_ERROR (default),
+ * L = sum_i |M r_i - e_i|^2 / |e_i|^2, or ODWF_NET_LOSS_RESIDUAL, L = sum_i |S M r_i - r_i|^2 / |r_i|^2
+ * (how far S M is from the identity on the training vectors; the e_i are not used). */
+#define ODWF_NET_LOSS_ERROR    0
+#define ODWF_NET_LOSS_RESIDUAL 1
+int odwf_net_set_loss(odwf_net_t* net, int mode);
+/* L (the selected loss) and dL/dconj(W) (host complex128, may be NULL). */
 int odwf_net_loss_grad(odwf_net_t* net, double* loss, double* grad, void* stream);
 /* steps Adam updates with learning rate lr on the stored pairs; losses[steps + 1] may be NULL. */
 int odwf_net_train(odwf_net_t* net, int steps, double lr, double* losses, void* stream);
@@ -282,7 +288,8 @@ int eofa_solve_learned(odwf_t* h, odwf_net_t* net, double m1, double m2, const v
 int eofa_solve_gcr(odwf_t* h, odwf_net_t* net, double m1, double m2, const void* b, void* x, int nvec, int truncate,
                    const odwf_solve_opts* opts, odwf_solve_stats* stats, void* stream);
 
-/* Autotuner: times the launch choices (tile: the default number of sites per CTA or twice it, as long
+/* Autotuner: times the launch choices (fifth-dimension form at Ns = 16: the structured recurrence or the
+ * dense Ns x Ns product; tile: the default number of sites per CTA or twice it, as long
  * as the CTA stays within 256 threads; grid size: one resident wave, one CTA per site group, two or
  * four waves; per-thread neighbour gathers or bulk-staged gathers) of the four fused kernels of the
  * CGNE iteration in precision prec on this handle's lattice and keeps the fastest for later calls.
@@ -293,7 +300,7 @@ int odwf_autotune(odwf_t* h, int prec, char* report, int report_len, void* strea
 /* Persisted autotuner choices: if the text file `path` holds an entry for this device name, lattice,
  * Ns and precision, its choices are applied (*hit = 1, no timing); otherwise odwf_autotune runs and
  * its choices are appended to the file as one line (*hit = 0). Returns ODWF_EINVAL if the file cannot
- * be appended to. Entries are plain text: device|LxxLyxLzxLt|Ns|prec|key:grid-mode:staged:tile,... */
+ * be appended to. Entries are plain text: device|LxxLyxLzxLt|Ns|prec|key:grid-mode:staged:tile:dense,... */
 int odwf_autotune_cache(odwf_t* h, int prec, const char* path, int* hit, void* stream);
 
 /* Kernel timing for measurement: while enabled, every launch of the library's kernels on this

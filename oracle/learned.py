@@ -18,8 +18,10 @@ M[U^g](G r) = G M[U] r for every gauge transform G. With W0 = 1, W1[0, mu] = W2[
 W1[0, 4+mu] = W2[0, 4+mu] = 1 + gamma_mu and the other channels zero, M is exactly the two-term
 Neumann series A^{-1} + 1/4 A^{-1} H A^{-1} H A^{-1} of S^{-1} = (A - 1/4 H A^{-1} H)^{-1}.
 
-Training loss over pairs (r_i, e_i = S^{-1} r_i): L = sum_i |M r_i - e_i|^2 / |e_i|^2.
-Gradients are Wirtinger derivatives dL/dconj(W) (the steepest-descent direction for complex W).
+Training loss over pairs (r_i, e_i = S^{-1} r_i): L = sum_i |M r_i - e_i|^2 / |e_i|^2 ("error" loss),
+or, needing no solves, L = sum_i |S M r_i - r_i|^2 / |r_i|^2 ("residual" loss: how far S M is from the
+identity on the training vectors). Gradients are Wirtinger derivatives dL/dconj(W) (the steepest-descent
+direction for complex W); for the residual loss dL/dconj(M r) = S^dag (S M r - r) / |r|^2.
 """
 from __future__ import annotations
 
@@ -125,29 +127,46 @@ class LearnedPreconditioner:
             gu = gu + sum(even * transport_adj(U, spin_mul(W.W1[c, d].conj().T, gh), d) for d in range(8))
         return self._AinvT(gu)
 
-    def loss_and_grad(self, rs, es):
-        """L = sum |M r - e|^2 / |e|^2 and its Wirtinger gradient dL/dconj(W) (as a Weights)."""
+    def _backprop(self, t, dl, G0, G1, G2):
+        """Add to G the Wirtinger gradient of a loss whose derivative along conj(M r) is dl."""
         sch, U, W = self.sch, self.U, self.W
-        even, odd = sch.even, sch.odd
-        G0 = np.zeros_like(W.W0)
-        G1 = np.zeros_like(W.W1)
-        G2 = np.zeros_like(W.W2)
-        L = 0.0
+        odd = sch.odd
+
         def outer(a, b):  # sum over sites, s and color of a_i conj(b_j)
             return np.einsum("nic,njc->ij", a.reshape(-1, 4, 3), b.conj().reshape(-1, 4, 3))
+        G0 += outer(dl, t["u"])
+        gy = 0.25 * self._AinvT(dl)
+        for c in range(W.C):
+            for d in range(8):
+                G2[c, d] += outer(gy, t["Tv"][c][d])
+            gv = sum(odd * transport_adj(U, spin_mul(W.W2[c, d].conj().T, gy), d) for d in range(8))
+            gh = self._AinvT(gv)
+            for d in range(8):
+                G1[c, d] += outer(gh, t["Tu"][d])
+
+    def loss_and_grad(self, rs, es):
+        """L = sum |M r - e|^2 / |e|^2 and its Wirtinger gradient dL/dconj(W) (as a Weights)."""
+        W, even = self.W, self.sch.even
+        G0, G1, G2 = np.zeros_like(W.W0), np.zeros_like(W.W1), np.zeros_like(W.W2)
+        L = 0.0
         for r, e in zip(rs, es):
             out, t = self.forward(r, keep=True)
             ne = np.vdot(e, e).real
             delta = (out - e) * even
             L += np.vdot(delta, delta).real / ne
-            dl = delta / ne                      # dL/dconj(out)
-            G0 += outer(dl, t["u"])
-            gy = 0.25 * self._AinvT(dl)
-            for c in range(W.C):
-                for d in range(8):
-                    G2[c, d] += outer(gy, t["Tv"][c][d])
-                gv = sum(odd * transport_adj(U, spin_mul(W.W2[c, d].conj().T, gy), d) for d in range(8))
-                gh = self._AinvT(gv)
-                for d in range(8):
-                    G1[c, d] += outer(gh, t["Tu"][d])
+            self._backprop(t, delta / ne, G0, G1, G2)   # dL/dconj(out) = delta / ne
+        return L, Weights(G0, G1, G2)
+
+    def residual_loss_and_grad(self, rs):
+        """L = sum |S M r - r|^2 / |r|^2 and its Wirtinger gradient (as a Weights)."""
+        sch, W, even = self.sch, self.W, self.sch.even
+        G0, G1, G2 = np.zeros_like(W.W0), np.zeros_like(W.W1), np.zeros_like(W.W2)
+        L = 0.0
+        for r in rs:
+            r = r * even
+            out, t = self.forward(r, keep=True)
+            nr = np.vdot(r, r).real
+            w = sch.S(out) - r
+            L += np.vdot(w, w).real / nr
+            self._backprop(t, sch.S_dag(w) / nr, G0, G1, G2)
         return L, Weights(G0, G1, G2)

@@ -34,7 +34,7 @@ EXPORTS = ["odwf_create", "odwf_destroy", "odwf_last_error", "odwf_set_gauge", "
            "odwf_net_num_params", "odwf_net_weights", "odwf_net_apply", "odwf_net_set_pairs", "odwf_net_loss_grad",
            "odwf_net_train", "eofa_solve_learned", "odwf_autotune", "eofa_solve_gcr", "eofa_term_spectrum",
            "hmc_gauge_action", "hmc_gauge_force", "hmc_momentum_update", "hmc_link_update", "hmc_kinetic",
-           "hmc_md", "odwf_autotune_cache"]
+           "hmc_md", "odwf_autotune_cache", "odwf_net_set_loss"]
 
 
 class OdwfError(RuntimeError):
@@ -136,6 +136,7 @@ def load_library(path: str = LIB_PATH):
     lib.odwf_net_apply.argtypes = [vp, d, d, vp, vp, i, vp]
     lib.odwf_net_set_pairs.argtypes = [vp, d, d, i, ctypes.POINTER(vp), ctypes.POINTER(vp), d, vp]
     lib.odwf_net_loss_grad.argtypes = [vp, dp, dp, vp]
+    lib.odwf_net_set_loss.argtypes = [vp, i]
     lib.odwf_net_train.argtypes = [vp, i, d, dp, vp]
     lib.eofa_solve_learned.argtypes = [vp, vp, d, d, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), vp]
     lib.eofa_solve_gcr.argtypes = [vp, vp, d, d, vp, vp, i, i, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), vp]
@@ -474,6 +475,10 @@ class Net:
         ep = (ctypes.c_void_p * n)(*[e.data_ptr() for e in es]) if es is not None else None
         self.lat._check(self.lib.odwf_net_set_pairs(self.n, float(m1), float(m2), n, rp, ep, float(tol),
                                                     _stream_ptr(stream)))
+
+    def set_loss(self, mode):
+        """"error" (|M r - e|^2/|e|^2, default) or "residual" (|S M r - r|^2/|r|^2)."""
+        self.lat._check(self.lib.odwf_net_set_loss(self.n, {"error": 0, "residual": 1}[mode]))
 
     def loss_grad(self, stream=None):
         import numpy as np

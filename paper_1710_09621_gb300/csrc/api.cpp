@@ -695,8 +695,8 @@ extern "C" int odwf_autotune(odwf_t* h, int prec, char* report, int report_len, 
         for (auto& l : log) all += l + "\n";
         for (auto& kv : h->tune) {
             char buf[128];
-            std::snprintf(buf, sizeof buf, "chosen key %d: grid-mode %d staged %d tile x%d\n", kv.first, kv.second.mode,
-                          kv.second.staged, kv.second.spbm);
+            std::snprintf(buf, sizeof buf, "chosen key %d: grid-mode %d staged %d tile x%d %s\n", kv.first,
+                          kv.second.mode, kv.second.staged, kv.second.spbm, kv.second.dense ? "dense" : "structured");
             all += buf;
         }
         std::strncpy(report, all.c_str(), report_len - 1);
@@ -753,9 +753,10 @@ extern "C" int odwf_autotune_cache(odwf_t* h, int prec, const char* path, int* h
                 if (end == std::string::npos) end = found.size();
                 int k = 0;
                 TuneChoice tc;
-                if (std::sscanf(found.substr(pos, end - pos).c_str(), "%d:%d:%d:%d", &k, &tc.mode, &tc.staged, &tc.spbm) != 4 ||
-                    tc.mode < 0 || tc.mode > 3 || tc.staged < 0 || tc.staged > 1 || tc.spbm < 1 || tc.spbm > 2 ||
-                    (k / 100000) % 10 != stg) {
+                const int nf = std::sscanf(found.substr(pos, end - pos).c_str(), "%d:%d:%d:%d:%d", &k, &tc.mode, &tc.staged,
+                                           &tc.spbm, &tc.dense);
+                if (nf < 4 || tc.mode < 0 || tc.mode > 3 || tc.staged < 0 || tc.staged > 1 || tc.spbm < 1 ||
+                    tc.spbm > 2 || tc.dense < 0 || tc.dense > 1 || (k / 100000) % 10 != stg) {
                     bad = true;
                     break;
                 }
@@ -776,8 +777,8 @@ extern "C" int odwf_autotune_cache(odwf_t* h, int prec, const char* path, int* h
     for (auto& kv : h->tune) {
         if ((kv.first / 100000) % 10 != stg) continue;
         char buf[64];
-        std::snprintf(buf, sizeof buf, "%s%d:%d:%d:%d", first ? "" : ",", kv.first, kv.second.mode, kv.second.staged,
-                      kv.second.spbm);
+        std::snprintf(buf, sizeof buf, "%s%d:%d:%d:%d:%d", first ? "" : ",", kv.first, kv.second.mode, kv.second.staged,
+                      kv.second.spbm, kv.second.dense);
         entry += buf;
         first = false;
     }

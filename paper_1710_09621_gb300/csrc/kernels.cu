@@ -930,16 +930,18 @@ static int launch_one(odwf_s* h, int parity, HopArgs a, cudaStream_t st) {
     const int base_key = ST * 100000 + HOP * 10000 + MIXHOP * 1000 + OWN * 100 + MIXOWN * 10 + EPI;
     bool stg = KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::CAN_STAGE && staged_ok(h, ST);
     int mode = 0;
+    bool force_dense = false;
     auto tuned = h->tune.find(base_key);
     if (tuned != h->tune.end()) {
         mode = tuned->second.mode;
+        force_dense = tuned->second.dense != 0;
         stg = KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::CAN_STAGE && staged_geom_ok(h, ST) && tuned->second.staged;
         // tile: a multiple of the default sites per CTA while the CTA stays within 256 threads
         if (tuned->second.spbm > 1 && spb * tuned->second.spbm * Ns <= 256) spb *= tuned->second.spbm;
     }
     // the structured fifth-dimension product: single-system per-thread-gather kernels at Ns = kStructNs
     const bool sn = KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::CAN_STRUCT && !stg && Ns == kStructNs &&
-                    a.sop != SOP_DENSE;
+                    a.sop != SOP_DENSE && !force_dense;
     const int occ = occupancy<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(h, stg ? 2 : (sn ? 4 : 0), &smem, spb);
     const int groups = (h->Vh + spb - 1) / spb;
     const int grid = grid_for_mode(h, mode, occ, groups, EPI != EPI_STORE);
@@ -1396,13 +1398,17 @@ int autotune_storage(odwf_s* h, int stg, const SCoef* c, cudaStream_t st, std::v
         float best = 1e30f;
         TuneChoice best_choice{};
         const int max_spbm = spb_for(h->Ns) * 2 * h->Ns <= 256 ? 2 : 1;
+        // the structured and the dense fifth-dimension product where both exist (Ns = kStructNs)
+        const int max_dense = (h->Ns == kStructNs && a.sop != SOP_DENSE) ? 1 : 0;
+        for (int dense = 0; dense <= max_dense; ++dense)
         for (int spbm = 1; spbm <= max_spbm; ++spbm)
-        for (int staged = 0; staged <= (can_stage ? 1 : 0); ++staged)
+        for (int staged = 0; staged <= (can_stage && !dense ? 1 : 0); ++staged)
             for (int mode = 0; mode < 4; ++mode) {
                 TuneChoice tc;
                 tc.mode = mode;
                 tc.staged = staged;
                 tc.spbm = spbm;
+                tc.dense = dense;
                 h->tune[base_key] = tc;
                 int rc = fill();
                 if (rc) return set_err(h, rc, "autotune: fill");
@@ -1418,8 +1424,8 @@ int autotune_storage(odwf_s* h, int stg, const SCoef* c, cudaStream_t st, std::v
                 cudaEventElapsedTime(&ms, e0, e1);
                 ms /= reps;
                 char buf[160];
-                std::snprintf(buf, sizeof buf, "%s storage %d tile x%d staged %d grid-mode %d: %.1f us", v.name, stg, spbm,
-                              staged, mode, 1e3 * ms);
+                std::snprintf(buf, sizeof buf, "%s storage %d %s tile x%d staged %d grid-mode %d: %.1f us", v.name, stg,
+                              dense ? "dense" : "structured", spbm, staged, mode, 1e3 * ms);
                 log.push_back(buf);
                 if (ms < best) {
                     best = ms;

@@ -12,6 +12,7 @@
 // so the rows it writes to shared memory are the rows it multiplies (no CTA barrier needed).
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -862,6 +863,10 @@ __global__ void k_resid_scale(const float* out, const float* e, float* delta, si
     }
 }
 
+__global__ void k_scale_f(float* x, size_t n, float c) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) x[i] *= c;
+}
+
 }  // namespace odwf
 
 // ================================================================================================
@@ -879,7 +884,7 @@ struct odwf_net_s {
     float *B0 = nullptr, *B1 = nullptr, *B2 = nullptr, *B3 = nullptr, *w0f = nullptr, *w0adj = nullptr;
     bool prepped = false;
     double cm1 = -1, cm2 = -1;
-    bool no_tc = false;      // ODWF_NO_TCGEN05=1: mma.sync layers only
+    bool use_tc = false;     // ODWF_TCGEN05=1: the tcgen05 1 -> 2 layer at Ns = 16 (default: mma.sync)
     double* mats = nullptr;  // transposed A^{-1} (2 Ns^2) then A^{-T} (2 Ns^2), FP64
     SCoef sc{};              // structured form of the same (for the s-mixing kernel; sc.dev unused)
     // FP32 half fields: u (even), v[C] (odd), t (even), gy (even), gh[C] (odd), delta (even)
@@ -888,10 +893,15 @@ struct odwf_net_s {
     float* partials = nullptr;
     int partials_n = 0;
     std::vector<float*> pairs;  // r_i, e_i (even, FP32)
-    std::vector<double> pair_ne;
+    std::vector<double> pair_ne;  // |e_i|^2
+    std::vector<double> pair_nr;  // |r_i|^2
+    int loss_mode = 0;            // ODWF_NET_LOSS_ERROR or ODWF_NET_LOSS_RESIDUAL
 };
 
 namespace {
+
+// S or S^dag in FP32 on even fields (defined with the preconditioned solver below)
+int schur32(odwf_s* h, const SCoef* c, const float* in, float* tmp, float* out, bool dag, cudaStream_t st);
 
 int net_err(odwf_net_s* n, int code, const std::string& msg) { return set_err(n ? n->h : nullptr, code, msg); }
 
@@ -987,7 +997,7 @@ int net_layer(odwf_net_s* n, int parity, int cin, int cout, const float* const* 
         if (h->prof) prof_end(h, key, st, ev0);
         return cuda_check(h, cudaGetLastError(), "k_net_layer");
     };
-    if (cin == 1 && cout == 2 && h->Ns == 16 && spb == 8 && !n->no_tc) {
+    if (cin == 1 && cout == 2 && h->Ns == 16 && spb == 8 && n->use_tc) {
         // the tcgen05 layer: its own shared-memory layout and a bounded wait (read by check_fault)
         a.fault = h->fault;
         h->staged_used = true;
@@ -998,12 +1008,23 @@ int net_layer(odwf_net_s* n, int parity, int cin, int cout, const float* const* 
             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tc);
             set_tc[bf16 ? 1 : 0] = true;
         }
-        int occ = 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, h->Ns * spb, smem_tc);
+        // resident CTAs per SM from the kernel's registers, its shared memory and its tensor-memory columns
+        static int occ_tc = 0;
+        if (occ_tc == 0) {
+            cudaFuncAttributes fa{};
+            int dev = 0, smem_sm = 0;
+            cudaFuncGetAttributes(&fa, fn);
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+            const int by_regs = fa.numRegs > 0 ? 65536 / (fa.numRegs * 128) : 1;
+            const int by_smem = (int)(smem_sm / (smem_tc + 1024));
+            const int by_tmem = 512 / (int)kTcCols;
+            occ_tc = std::max(1, std::min(by_regs, std::min(by_smem, by_tmem)));
+        }
         const int key = 2000000 + (bf16 ? 1000 : 0) + cin * 100 + cout * 10 + (own ? 1 : 0);
         cudaEvent_t ev0 = nullptr;
         if (h->prof) prof_begin(h, key, st, &ev0);
-        fn<<<grid_for_groups(h, occ < 1 ? 1 : occ), blk, smem_tc, st>>>(a);
+        fn<<<grid_for_groups(h, occ_tc), blk, smem_tc, st>>>(a);
         if (h->prof) prof_end(h, key, st, ev0);
         return cuda_check(h, cudaGetLastError(), "k_net_layer12_tc");
     }
@@ -1108,11 +1129,24 @@ int net_loss_grad(odwf_net_s* n, double* loss_out, cudaStream_t st) {
         const float* in2[2] = {v0, v1};
         float* o[1] = {out};
         if ((rc = net_layer(n, 0, C, 1, in2, n->B1, u, n->w0f, 0, o, Ainv, 0.25f, st))) return rc;
-        const double ne = n->pair_ne[i];
-        k_resid_scale<<<rb, 256, 0, st>>>(out, e, delta, nreal, (float)(1.0 / ne), n->partials);
-        if ((rc = cuda_check(h, cudaGetLastError(), "k_resid_scale"))) return rc;
         double* lsum = n->grad + n->P * 2;  // scratch double after the gradient
-        k_sum_partials<<<1, 32, 0, st>>>(n->partials, rb, 1, lsum + i, 0);
+        if (n->loss_mode == ODWF_NET_LOSS_RESIDUAL) {
+            // w = S M r - r (gy), |w|^2 to lsum; delta = S^dag w / |r|^2 = dL/dconj(M r)
+            const SCoef* c = get_coef(h, n->cm1, n->cm2);
+            if (!c) return ODWF_EINVAL;
+            if ((rc = schur32(h, c, out, gh1, gh0, false, st))) return rc;
+            k_resid_scale<<<rb, 256, 0, st>>>(gh0, r, gy, nreal, 1.f, n->partials);
+            if ((rc = cuda_check(h, cudaGetLastError(), "k_resid_scale"))) return rc;
+            k_sum_partials<<<1, 32, 0, st>>>(n->partials, rb, 1, lsum + i, 0);
+            if ((rc = schur32(h, c, gy, gh1, delta, true, st))) return rc;
+            k_scale_f<<<rb, 256, 0, st>>>(delta, nreal, (float)(1.0 / n->pair_nr[i]));
+            if ((rc = cuda_check(h, cudaGetLastError(), "k_scale_f"))) return rc;
+        } else {
+            const double ne = n->pair_ne[i];
+            k_resid_scale<<<rb, 256, 0, st>>>(out, e, delta, nreal, (float)(1.0 / ne), n->partials);
+            if ((rc = cuda_check(h, cudaGetLastError(), "k_resid_scale"))) return rc;
+            k_sum_partials<<<1, 32, 0, st>>>(n->partials, rb, 1, lsum + i, 0);
+        }
         // G0 = sum delta (x) conj(u)
         const float* gin[1] = {u};
         const float* gdl[1] = {delta};
@@ -1141,7 +1175,8 @@ int net_loss_grad(odwf_net_s* n, double* loss_out, cudaStream_t st) {
                          "grad H2D")))
         return rc;
     double L = 0.0;
-    for (size_t i = 0; i < n->pairs.size() / 2; ++i) L += gh[(size_t)n->P * 2 + i] / n->pair_ne[i];
+    for (size_t i = 0; i < n->pairs.size() / 2; ++i)
+        L += gh[(size_t)n->P * 2 + i] / (n->loss_mode == ODWF_NET_LOSS_RESIDUAL ? n->pair_nr[i] : n->pair_ne[i]);
     if (loss_out) *loss_out = L;
     return cuda_check(h, cudaStreamSynchronize(st), "sync");
 }
@@ -1158,7 +1193,7 @@ extern "C" int odwf_net_create(odwf_t* h, int channels, odwf_net_t** out) {
     odwf_net_s* n = new odwf_net_s();
     n->h = h;
     n->C = channels;
-    if (const char* e = std::getenv("ODWF_NO_TCGEN05")) n->no_tc = (e[0] == '1');
+    if (const char* e = std::getenv("ODWF_TCGEN05")) n->use_tc = (e[0] == '1');
     n->P = 16 + 2 * channels * 8 * 16;
     const int C = channels;
     int rc = ODWF_OK;
@@ -1272,6 +1307,7 @@ extern "C" int odwf_net_set_pairs(odwf_net_t* n, double m1, double m2, int npair
     for (float* p : n->pairs) cudaFree(p);
     n->pairs.clear();
     n->pair_ne.clear();
+    n->pair_nr.clear();
     odwf_solve_opts so{tol, 100000, ODWF_PREC_SINGLE, 0.01, 0.0};
     for (int i = 0; i < npairs; ++i) {
         float *rf = nullptr, *ef = nullptr;
@@ -1291,12 +1327,20 @@ extern "C" int odwf_net_set_pairs(odwf_net_t* n, double m1, double m2, int npair
             if ((rc = launch_convert(h, h->ws.x_e, ST_DOUBLE, nullptr, ef, ST_FLOAT, nullptr, st))) return rc;
         }
         if ((rc = launch_norm2(h, ef, ST_FLOAT, nullptr, 0, st))) return rc;
+        if ((rc = launch_norm2(h, rf, ST_FLOAT, nullptr, 1, st))) return rc;
         CGState hs;
         if ((rc = cuda_check(h, cudaMemcpyAsync(&hs, h->state, sizeof(CGState), cudaMemcpyDeviceToHost, st), "D2H")))
             return rc;
         if ((rc = cuda_check(h, cudaStreamSynchronize(st), "sync"))) return rc;
         n->pair_ne.push_back(hs.result[0]);
+        n->pair_nr.push_back(hs.result[1]);
     }
+    return ODWF_OK;
+}
+
+extern "C" int odwf_net_set_loss(odwf_net_t* n, int mode) {
+    if (!n || (mode != ODWF_NET_LOSS_ERROR && mode != ODWF_NET_LOSS_RESIDUAL)) return ODWF_EINVAL;
+    n->loss_mode = mode;
     return ODWF_OK;
 }
 

@@ -126,6 +126,7 @@ struct TuneChoice {
     int mode = 0;
     int staged = 0;
     int spbm = 1;
+    int dense = 0;  // 1: the dense Ns x Ns fifth-dimension product even where the structured one applies
 };
 
 struct SCoef {

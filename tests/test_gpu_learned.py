@@ -98,6 +98,24 @@ def test_net_loss_and_gradient(env):
     assert _rel(g, Go.flat()) < 5e-2
 
 
+def test_net_residual_loss_and_gradient(env):
+    """The residual loss |S M r - r|^2/|r|^2 (no solves) and its gradient against the oracle."""
+    binding, lat, op, U, om = env
+    net = binding.Net(lat, 2)
+    W = _rand_weights(2, 8, scale=0.2)
+    net.set_weights(W.flat())
+    net.set_loss("residual")
+    sch = solver.Schur(op, M1, M2)
+    rs = [inputs.gaussian_spinor5(DIMS, NS, 14 + i) for i in range(2)]
+    es = [inputs.gaussian_spinor5(DIMS, NS, 24 + i) for i in range(2)]  # not used by this loss
+    net.set_pairs([torch.from_numpy(r).cuda() for r in rs], M1, M2, es=[torch.from_numpy(e).cuda() for e in es])
+    L, g = net.loss_grad()
+    Lo, Go = learned.LearnedPreconditioner(sch, W).residual_loss_and_grad([r * sch.even for r in rs])
+    assert abs(L - Lo) < 2e-2 * Lo
+    assert _rel(g, Go.flat()) < 5e-2
+    net.close()
+
+
 def test_train_and_solve(env):
     """Pairs from the library's solver; Adam lowers the loss; the preconditioned solve meets 1e-10."""
     binding, lat, op, U, om = env
@@ -159,13 +177,13 @@ def test_gcr_rejects_bad_basis_and_reports_noconv(env):
     assert st["status"] == binding.ODWF_ENOCONV and st["iters"] == 3 and st["true_residual"] > 1e-10
 
 
-@pytest.mark.parametrize("no_tc", ["0", "1"])
-def test_net_ns16_tensor_memory_layer(no_tc, monkeypatch):
-    """At Ns = 16 the 1 -> 2 layer (forward, and the first adjoint layer) runs on the fifth-generation
-    tensor cores: tcgen05.mma with FP32 accumulators in tensor memory; ODWF_NO_TCGEN05=1 selects the
-    mma.sync layer. Both against the oracle (BF16 tolerance 2e-2 outputs, 5e-2 weight gradients), and the
-    preconditioned solve meets the FP64 true residual."""
-    monkeypatch.setenv("ODWF_NO_TCGEN05", no_tc)
+@pytest.mark.parametrize("use_tc", ["1", "0"])
+def test_net_ns16_tensor_memory_layer(use_tc, monkeypatch):
+    """At Ns = 16 the 1 -> 2 layer (forward, and the first adjoint layer) can run on the fifth-generation
+    tensor cores (ODWF_TCGEN05=1): tcgen05.mma with FP32 accumulators in tensor memory; the default is
+    the mma.sync layer. Both against the oracle (BF16 tolerance 2e-2 outputs, 5e-2 weight gradients), and
+    the preconditioned solve meets the FP64 true residual."""
+    monkeypatch.setenv("ODWF_TCGEN05", use_tc)
     from paper_1710_09621_gb300 import build
     build.build()
     from paper_1710_09621_gb300 import binding

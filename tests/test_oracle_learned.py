@@ -104,3 +104,35 @@ def test_training_step_reduces_loss(setup):
             break
         t *= 0.5
     assert best < 0.99 * L0, (L0, best)
+
+
+def test_residual_loss_gradient_finite_difference(setup):
+    """Residual loss L = sum |S M r - r|^2/|r|^2: Wirtinger gradient vs central differences, and
+    with the Neumann weights L equals the closed form |(1/4 A^{-1} H A^{-1} H)^2 r'|-type remainder
+    computed independently as |S M r - r|^2 from the Schur pieces."""
+    op, sch = setup
+    W = _rand_weights(2, 13)
+    rs = [gaussian_spinor5(DIMS, NS, 50 + i) * sch.even for i in range(2)]
+    L, G = learned.LearnedPreconditioner(sch, W).residual_loss_and_grad(rs)
+    flat, gflat = W.flat(), G.flat()
+    rng = np.random.default_rng(1)
+    h = 1e-6
+
+    def L_at(v):
+        return learned.LearnedPreconditioner(sch, learned.Weights.from_flat(v, 2)).residual_loss_and_grad(rs)[0]
+
+    for idx in rng.choice(len(flat), 8, replace=False):
+        for part, unit in (("re", 1.0), ("im", 1j)):
+            vp, vm = flat.copy(), flat.copy()
+            vp[idx] += h * unit
+            vm[idx] -= h * unit
+            fd = (L_at(vp) - L_at(vm)) / (2 * h)
+            an = 2 * (gflat[idx].real if part == "re" else gflat[idx].imag)
+            assert abs(fd - an) < 1e-6 * max(1.0, abs(an)), (idx, part, fd, an)
+    # Neumann weights: M = (1 + K) A^{-1} with K = 1/4 A^{-1} H A^{-1} H, S = A (1 - K), so
+    # S M - 1 = A (1 - K)(1 + K) A^{-1} - 1 = -A K^2 A^{-1}
+    Mn = learned.LearnedPreconditioner(sch, learned.neumann_weights(C=2))
+    Ln, _ = Mn.residual_loss_and_grad(rs)
+    K = lambda v: 0.25 * sch.Ainv(sch.hop_to(sch.Ainv(sch.hop_to(v, sch.odd)), sch.even))
+    ref = sum(np.linalg.norm(sch.A(K(K(sch.Ainv(r))))) ** 2 / np.linalg.norm(r) ** 2 for r in rs)
+    assert abs(Ln - ref) < 1e-12 * ref
