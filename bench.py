@@ -370,6 +370,22 @@ def md_step(lat, binding, inputs, dims, U, opts, opts_ref, beta, dtau, rank):
                     "force_s": t_f, "force_iters": st_f["iters"],
                     "action_rel_err_vs_tight": abs(S - Sr) / abs(Sr),
                     "force_rel_err_vs_tight": float(torch.linalg.vector_norm(F - Fr) / torch.linalg.vector_norm(Fr))})
+    # the chosen method on the EOFA path: the same action and force solves with CGNE on S M, the network
+    # (Neumann-initialised: no training cost) attached to the handle
+    net = binding.Net(lat, channels=2)
+    lat.set_preconditioner(net)
+    lopts = binding.solve_opts(tol=opts.tol, prec="single", delta=1e-3)
+    for t, phi, r in zip(terms, phis, rec):
+        ta = time.perf_counter()
+        S_n, st_an = lat.action(t, phi, opts=lopts)
+        t_an = time.perf_counter() - ta
+        tf = time.perf_counter()
+        F_n, st_fn = lat.force(t, phi, opts=lopts)
+        t_fn = time.perf_counter() - tf
+        r.update({"net_action_s": t_an, "net_action_iters": st_an["iters"], "net_force_s": t_fn,
+                  "net_force_iters": st_fn["iters"]})
+    lat.set_preconditioner(None)
+    net.close()
     K0 = lat.kinetic(P)  # momenta after the fermion kicks; the gauge kick and link update follow
     Sg0 = lat.gauge_action(Ux, beta)
     Fg = lat.gauge_force(Ux, beta)
@@ -411,10 +427,18 @@ def hmc_trajectory(lat, binding, inputs, dims, U, opts, beta, rank, steps=PAPER_
         phis.append(phi)
         hb_iters += hb["iters"]
     t_hb = time.perf_counter() - t0
-    st = lat.md(Ux, P, beta, terms, phis, paper_levels(len(terms)), list(steps), tau=1.0, opts=opts)
+    # the force and action solves with CGNE on S M (Neumann-initialised network attached)
+    net = binding.Net(lat, channels=2)
+    lat.set_preconditioner(net)
+    st = lat.md(Ux, P, beta, terms, phis, paper_levels(len(terms)), list(steps), tau=1.0,
+                opts=binding.solve_opts(tol=opts.tol, prec="single", delta=1e-3))
     torch.cuda.synchronize()
+    lat.set_preconditioner(None)
+    net.close()
     lat.set_gauge(U)
     return {"dims": list(dims), "beta": beta, "steps_k0_k1_k2": list(steps),
+            "solver": "heat-bath: batched mixed-precision CGNE over the poles; MD forces and actions: CGNE on S M "
+                      "with the Neumann-initialised network (odwf_set_preconditioner)",
             "levels": paper_levels(len(terms)), "heatbath_seconds": t_hb, "heatbath_iters": hb_iters,
             "md_seconds": st["seconds"], "seconds": time.perf_counter() - t0, "dH": st["dH"],
             "force_evals": st["force_evals"][:3], "link_updates": st["link_updates"], "md_cg_iters": st["cg_iters"],
@@ -436,6 +460,8 @@ def main():
     ap.add_argument("--train-steps", type=int, default=200)
     ap.add_argument("--lr", type=float, default=5e-3, help="Adam learning rate of the network training")
     ap.add_argument("--pairs", type=int, default=8, help="training pairs (r, S^{-1} r) from the plain solver")
+    ap.add_argument("--train-loss", default="residual", choices=["residual", "error"],
+                    help="network training loss: |S M r - r|^2/|r|^2 (default) or |M r - e|^2/|e|^2")
     ap.add_argument("--method", default="learned", choices=["learned", "gcr", "cgne"],
                     help="timed solver: learned-preconditioned CGNE (default), flexible GCR right-preconditioned "
                          "by the learned network, or plain mixed-precision CGNE")
@@ -502,6 +528,7 @@ def main():
     if args.method in ("learned", "gcr"):
         from paper_1710_09621_gb300.binding import Net
         net = Net(lat, channels=2)
+        net.set_loss(args.train_loss)
         rs = [torch.from_numpy(inputs.gaussian_spinor5(DIMS, NS, inputs.seed_for(4, i))).to(dev)
               for i in range(args.pairs)]
         torch.cuda.synchronize()
@@ -510,7 +537,8 @@ def main():
         t1 = time.perf_counter()
         losses = net.train(args.train_steps, args.lr)
         t2 = time.perf_counter()
-        learned_setup = {"pairs": len(rs), "pair_seconds": t1 - t0, "train_steps": args.train_steps, "lr": args.lr,
+        learned_setup = {"pairs": len(rs), "loss": args.train_loss, "pair_seconds": t1 - t0,
+                         "train_steps": args.train_steps, "lr": args.lr,
                          "train_seconds": t2 - t1, "loss_first": float(losses[0]), "loss_last": float(losses[-1])}
         del rs
         lopts = solve_opts(tol=TOL, prec="single", delta=1e-3)

@@ -268,6 +268,12 @@ int odwf_net_set_loss(odwf_net_t* net, int mode);
 int odwf_net_loss_grad(odwf_net_t* net, double* loss, double* grad, void* stream);
 /* steps Adam updates with learning rate lr on the stored pairs; losses[steps + 1] may be NULL. */
 int odwf_net_train(odwf_net_t* net, int steps, double lr, double* losses, void* stream);
+/* Attach net (created on h) so that the single-system solves of eofa_action, eofa_force and hmc_md use
+ * the network-preconditioned CGNE of eofa_solve_learned (FP32 inner cycles restarted from the FP64
+ * residual whenever it has dropped by opts->delta; opts->prec is not used) instead of plain CGNE; the
+ * network applies the fifth-dimension inverse of each solve's own masses, its weights are shared. NULL
+ * detaches. The heat-bath keeps the batched plain solver for its poles. Not in the paper. */
+int odwf_set_preconditioner(odwf_t* h, odwf_net_t* net);
 /* H_T(m1, m2) x = b like eofa_solve, with CGNE on S M (right preconditioning by the network, the
  * iterate accumulating x = M y directly), FP32 inner cycles restarted from the FP64 residual
  * whenever it has dropped by opts->delta. */

@@ -34,7 +34,7 @@ EXPORTS = ["odwf_create", "odwf_destroy", "odwf_last_error", "odwf_set_gauge", "
            "odwf_net_num_params", "odwf_net_weights", "odwf_net_apply", "odwf_net_set_pairs", "odwf_net_loss_grad",
            "odwf_net_train", "eofa_solve_learned", "odwf_autotune", "eofa_solve_gcr", "eofa_term_spectrum",
            "hmc_gauge_action", "hmc_gauge_force", "hmc_momentum_update", "hmc_link_update", "hmc_kinetic",
-           "hmc_md", "odwf_autotune_cache", "odwf_net_set_loss"]
+           "hmc_md", "odwf_autotune_cache", "odwf_net_set_loss", "odwf_set_preconditioner"]
 
 
 class OdwfError(RuntimeError):
@@ -137,6 +137,7 @@ def load_library(path: str = LIB_PATH):
     lib.odwf_net_set_pairs.argtypes = [vp, d, d, i, ctypes.POINTER(vp), ctypes.POINTER(vp), d, vp]
     lib.odwf_net_loss_grad.argtypes = [vp, dp, dp, vp]
     lib.odwf_net_set_loss.argtypes = [vp, i]
+    lib.odwf_set_preconditioner.argtypes = [vp, vp]
     lib.odwf_net_train.argtypes = [vp, i, d, dp, vp]
     lib.eofa_solve_learned.argtypes = [vp, vp, d, d, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), vp]
     lib.eofa_solve_gcr.argtypes = [vp, vp, d, d, vp, vp, i, i, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), vp]
@@ -382,6 +383,11 @@ class ODWF:
         buf = ctypes.create_string_buffer(8192)
         self._check(self.lib.odwf_autotune(self.h, _PREC[prec], buf, 8192, _stream_ptr(stream)))
         return buf.value.decode()
+
+    def set_preconditioner(self, net):
+        """Attach a Net (or None) for the solves of action, force and the MD trajectory."""
+        self._check(self.lib.odwf_set_preconditioner(self.h, net.n if net is not None else None))
+        self._net = net  # keep it alive while attached
 
     def autotune_cached(self, path, prec="single", stream=None):
         """Apply the choices stored in `path` for this device, lattice and precision, or tune and append

@@ -357,11 +357,14 @@ static int contract(odwf_s* h, int chir, const double* w, const void* phi, void*
     return cuda_check(h, cudaGetLastError(), "k_contract");
 }
 
+// chi = H_T(m1, m2)^{-1} Omega P phi into ws.x_e / ws.x_o: plain mixed-precision CGNE, or, with a
+// network attached to the handle (odwf_set_preconditioner), CGNE on S M
 static int term_solve(odwf_s* h, const eofa_term* t, double m1, double m2, const void* phi,
                       const odwf_solve_opts* opts, odwf_solve_stats* stats, cudaStream_t st) {
     int rc = ensure_workspace(h, ST_DOUBLE);
     if (rc) return rc;
     if ((rc = embed(h, t, phi, st))) return rc;
+    if (h->net) return learned_solve(h, h->net, m1, m2, nullptr, nullptr, opts, stats, st);
     return solve_core(h, m1, m2, opts, stats, st);
 }
 

@@ -884,7 +884,7 @@ struct odwf_net_s {
     float *B0 = nullptr, *B1 = nullptr, *B2 = nullptr, *B3 = nullptr, *w0f = nullptr, *w0adj = nullptr;
     bool prepped = false;
     double cm1 = -1, cm2 = -1;
-    bool use_tc = false;     // ODWF_TCGEN05=1: the tcgen05 1 -> 2 layer at Ns = 16 (default: mma.sync)
+    bool use_tc = true;      // the tcgen05 1 -> 2 layer at Ns = 16 (ODWF_TCGEN05=0: the mma.sync layer)
     double* mats = nullptr;  // transposed A^{-1} (2 Ns^2) then A^{-T} (2 Ns^2), FP64
     SCoef sc{};              // structured form of the same (for the s-mixing kernel; sc.dev unused)
     // FP32 half fields: u (even), v[C] (odd), t (even), gy (even), gh[C] (odd), delta (even)
@@ -1252,6 +1252,7 @@ extern "C" int odwf_net_create(odwf_t* h, int channels, odwf_net_t** out) {
 
 extern "C" int odwf_net_destroy(odwf_net_t* n) {
     if (!n) return ODWF_OK;
+    if (n->h && n->h->net == n) n->h->net = nullptr;  // detach from the handle's EOFA solves
     void* ps[] = {n->W, n->m1, n->m2, n->grad, n->B0, n->B1, n->B2, n->B3, n->w0f, n->w0adj, n->mats, n->partials};
     for (void* p : ps) cudaFree(p);
     for (float* p : n->f) cudaFree(p);
@@ -1424,7 +1425,8 @@ int schur_start(odwf_s* h, const SCoef* c, const void* b, double* bnorm2, double
     Workspace& w = h->ws;
     const size_t b64 = half_elems_bytes(h, ST_DOUBLE);
     int rc;
-    if ((rc = launch_pack5(h, (const double*)b, w.b_e, w.b_o, ST_DOUBLE, 1, st))) return rc;
+    // b == nullptr: b' is already packed into ws.b_e / ws.b_o (the EOFA terms' right-hand sides)
+    if (b && (rc = launch_pack5(h, (const double*)b, w.b_e, w.b_o, ST_DOUBLE, 1, st))) return rc;
     if ((rc = launch_norm2(h, w.b_e, ST_DOUBLE, nullptr, 0, st))) return rc;
     if ((rc = launch_norm2(h, w.b_o, ST_DOUBLE, nullptr, 1, st))) return rc;
     if ((rc = launch_smix(h, ST_DOUBLE, w.b_o, w.t64, coef_mat(c, 2, h->Ns), 1.0, st, nullptr, nullptr, c, SOP_AINV)))
@@ -1478,7 +1480,8 @@ int schur_finish(odwf_s* h, const SCoef* c, void* x, double bnorm2, double* res,
     r2.out = w.t64;
     r2.slot = 1;
     if ((rc = launch_hop(h, ST_DOUBLE, 1, false, true, true, EPI_RESID, r2, st))) return rc;
-    if ((rc = launch_unpack5(h, w.x_e, w.x_o, (double*)x, ST_DOUBLE, 0, st))) return rc;
+    // x == nullptr: the solution stays in ws.x_e / ws.x_o
+    if (x && (rc = launch_unpack5(h, w.x_e, w.x_o, (double*)x, ST_DOUBLE, 0, st))) return rc;
     if ((rc = read_state(h, st))) return rc;
     *res = std::sqrt((h->state_host->result[0] + h->state_host->result[1]) / bnorm2);
     return ODWF_OK;
@@ -1508,12 +1511,30 @@ int schur32(odwf_s* h, const SCoef* c, const float* in, float* tmp, float* out, 
 
 }  // namespace
 
+namespace odwf {
+// The network-preconditioned CGNE of eofa_solve_learned with b (ABI field) and x (ABI field) optional:
+// b == nullptr takes b' = R5 g5 b already packed into ws.b_e / ws.b_o, x == nullptr leaves the solution
+// in ws.x_e / ws.x_o (the layout every EOFA term call reads).
+int learned_solve(odwf_s* h, odwf_net_s* n, double m1, double m2, const void* b, void* x,
+                  const odwf_solve_opts* opts_in, odwf_solve_stats* stats, cudaStream_t st);
+}  // namespace odwf
+
 extern "C" int eofa_solve_learned(odwf_t* h, odwf_net_t* n, double m1, double m2, const void* b, void* x,
                                   const odwf_solve_opts* opts_in, odwf_solve_stats* stats, void* stream) {
     if (!h || !n || !b || !x || n->h != h) return set_err(h, ODWF_EINVAL, "bad argument");
     if (!(m1 > 0.0 && m1 <= 1.0) || !(m2 > 0.0 && m2 <= 1.0)) return set_err(h, ODWF_EINVAL, "masses must lie in (0, 1]");
+    return odwf::learned_solve(h, n, m1, m2, b, x, opts_in, stats, (cudaStream_t)stream);
+}
+
+extern "C" int odwf_set_preconditioner(odwf_t* h, odwf_net_t* n) {
+    if (!h || (n && n->h != h)) return set_err(h, ODWF_EINVAL, "the network belongs to another handle");
+    h->net = n;
+    return ODWF_OK;
+}
+
+int odwf::learned_solve(odwf_s* h, odwf_net_s* n, double m1, double m2, const void* b, void* x,
+                        const odwf_solve_opts* opts_in, odwf_solve_stats* stats, cudaStream_t st) {
     const auto t0 = std::chrono::steady_clock::now();
-    cudaStream_t st = (cudaStream_t)stream;
     odwf_solve_opts o{1e-10, 100000, ODWF_PREC_SINGLE, 1e-3, 0.0};
     if (opts_in) o = *opts_in;
     int rc = ensure_workspace(h, ST_DOUBLE);

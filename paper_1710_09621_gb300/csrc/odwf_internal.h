@@ -195,6 +195,9 @@ struct odwf_s {
     odwf::HopArgs* bargs = nullptr;
     int bargs_cap = 0;
     cudaStream_t cap_stream = nullptr;   // non-default stream used only to capture CUDA graphs
+    // network whose preconditioned CGNE replaces plain CGNE in the single-system solves of the EOFA
+    // term calls (odwf_set_preconditioner); not owned
+    struct odwf_net_s* net = nullptr;
     // flexible-GCR basis and work fields, kept between calls; released by gcr_free at destroy
     void* gcr = nullptr;
     void (*gcr_free)(void*) = nullptr;
@@ -204,6 +207,8 @@ struct odwf_s {
     std::vector<ProfRec> prof_recs;
     std::vector<cudaEvent_t> prof_pool;
 };
+
+struct odwf_net_s;
 
 namespace odwf {
 
@@ -260,6 +265,11 @@ int launch_gauge(odwf_s* h, const double* U, cudaStream_t st);
 int launch_init_state(odwf_s* h, cudaStream_t st);
 void prof_begin(odwf_s* h, int key, cudaStream_t st, cudaEvent_t* a);
 void prof_end(odwf_s* h, int key, cudaStream_t st, cudaEvent_t a);
+
+// network-preconditioned CGNE (learned.cu): b / x are ABI fields, or null for b' packed in ws.b_e / b_o
+// and x left in ws.x_e / x_o
+int learned_solve(odwf_s* h, odwf_net_s* n, double m1, double m2, const void* b, void* x,
+                  const odwf_solve_opts* opts, odwf_solve_stats* stats, cudaStream_t st);
 
 // field helpers for EOFA (eofa.cu)
 // F (accumulate = 0) or F += coef F_term (accumulate = 1), F^a_mu(x) = -dS/dw^a of one EOFA term

@@ -179,9 +179,9 @@ def test_gcr_rejects_bad_basis_and_reports_noconv(env):
 
 @pytest.mark.parametrize("use_tc", ["1", "0"])
 def test_net_ns16_tensor_memory_layer(use_tc, monkeypatch):
-    """At Ns = 16 the 1 -> 2 layer (forward, and the first adjoint layer) can run on the fifth-generation
-    tensor cores (ODWF_TCGEN05=1): tcgen05.mma with FP32 accumulators in tensor memory; the default is
-    the mma.sync layer. Both against the oracle (BF16 tolerance 2e-2 outputs, 5e-2 weight gradients), and
+    """At Ns = 16 the 1 -> 2 layer (forward, and the first adjoint layer) runs on the fifth-generation
+    tensor cores: tcgen05.mma with FP32 accumulators in tensor memory; ODWF_TCGEN05=0 selects the
+    mma.sync layer. Both against the oracle (BF16 tolerance 2e-2 outputs, 5e-2 weight gradients), and
     the preconditioned solve meets the FP64 true residual."""
     monkeypatch.setenv("ODWF_TCGEN05", use_tc)
     from paper_1710_09621_gb300 import build
@@ -215,3 +215,28 @@ def test_net_ns16_tensor_memory_layer(use_tc, monkeypatch):
     net.close()
     neu.close()
     lat.close()
+
+
+def test_eofa_terms_with_attached_network(env):
+    """With a network attached (odwf_set_preconditioner) the EOFA action and force solve with CGNE on
+    S M; they still equal the oracle's (action 1e-10, force 1e-9), with fewer iterations than plain CGNE."""
+    from oracle import eofa as oeofa
+    binding, lat, op, U, om = env
+    phi = inputs.gaussian_spinor(DIMS, 61)
+    t = oeofa.Term(-1, 0.05, 0.05, 0.1)
+    spec = binding.TermSpec(t.chirality, t.m3, t.m4, t.m_den)
+    o = binding.solve_opts(tol=1e-12, prec="single", delta=1e-3)
+    S0, st0 = lat.action(spec, torch.from_numpy(phi).cuda(), opts=o)
+    net = binding.Net(lat, 2)
+    lat.set_preconditioner(net)
+    try:
+        S1, st1 = lat.action(spec, torch.from_numpy(phi).cuda(), opts=o)
+        F1, _ = lat.force(spec, torch.from_numpy(phi).cuda(), opts=o)
+    finally:
+        lat.set_preconditioner(None)
+        net.close()
+    So, _ = oeofa.action(op, t, phi, tol=1e-12)
+    Fo, _ = oeofa.force(op, t, phi, tol=1e-12)
+    assert abs(S1 - So) < 1e-10 * abs(So) and abs(S0 - So) < 1e-10 * abs(So)
+    assert _rel(F1.cpu().numpy(), Fo) < 1e-9
+    assert st1["iters"] < st0["iters"], (st1["iters"], st0["iters"])
