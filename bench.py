@@ -132,7 +132,8 @@ class ClockSampler:
 
 
 # algorithmic bytes per launch of the fused hopping kernels (per 5D half-site: spinor reads and
-# writes of 24 reals, links 8 x 18 reals per 4D half-site shared by Ns slices)
+# writes of 24 reals, links 8 x 18 reals per 4D half-site shared by Ns slices; 8 x 12 for the two-slice
+# kernels, which store two rows of each SU(3) link)
 def alg_bytes(key, Vh, Ns):
     if key >= 4000000:  # layout / vector kernels: kind, first and second storage (0 FP64, 1 FP32, 2 FP16)
         kind, s1, s2 = (key // 100) % 10, (key // 10) % 10, key % 10
@@ -157,6 +158,8 @@ def alg_bytes(key, Vh, Ns):
         fout = 48 if (bf16 and cout == 2) else 96
         return Vh * Ns * (fin * cin + fout * cout + 96 * own) + Vh * 8 * 18 * 4
     st = (key // 100000) % 10
+    pair = st >= 5                     # two-slice kernels: links stored as two rows (12 reals)
+    st -= 5 if pair else 0
     hop, mixhop, own, mixown, epi = (key // 10000) % 10, (key // 1000) % 10, (key // 100) % 10, (key // 10) % 10, key % 10
     rb = {0: 8, 1: 4, 2: 2}[st]        # bytes per real of the spinor storage
     lb = 8 if st == 0 else 4           # link storage
@@ -176,7 +179,7 @@ def alg_bytes(key, Vh, Ns):
         fields += 1
     by = n5 * fields * (24 * rb + scale)
     if hop:
-        by += Vh * 8 * 18 * lb
+        by += Vh * 8 * (12 if pair else 18) * lb
     return by
 
 
@@ -192,8 +195,12 @@ def kernel_name(key):
     if key >= 2000000:
         bf = ",bf16" if (key // 1000) % 10 else ""
         return f"k_net_layer<cin={(key // 100) % 10},cout={(key // 10) % 10}{',own' if key % 10 else ''}{bf}>"
-    st = ["fp64", "fp32", "fp16"][(key // 100000) % 10]
-    staged = "staged," if key >= 1000000 else ""
+    sd = (key // 100000) % 10
+    st = ["fp64", "fp32", "fp16"][sd % 5]
+    if sd >= 5:
+        staged = "two-slice bulk," if key >= 1000000 else "two-slice,"
+    else:
+        staged = "staged," if key >= 1000000 else ""
     hop, mixhop, own, mixown, epi = (key // 10000) % 10, (key // 1000) % 10, (key // 100) % 10, (key // 10) % 10, key % 10
     kind = {(1, 1, 0, 0): "hop+A^-1", (1, 0, 1, 1): "hop+A*own", (1, 1, 1, 0): "hop+own+A^-1",
             (1, 0, 1, 0): "hop+own", (0, 0, 1, 1): "s-mix"}.get((hop, mixhop, own, mixown), "hop")
@@ -445,6 +452,108 @@ def hmc_trajectory(lat, binding, inputs, dims, U, opts, beta, rank, steps=PAPER_
             "K0": st["K0"], "K1": st["K1"], "Sg0": st["Sg0"], "Sg1": st["Sg1"], "Sf0": st["Sf0"], "Sf1": st["Sf1"]}
 
 
+def config4(args):
+    """The learned preconditioner trained across seeded gauge configurations and evaluated on held-out ones
+    (32^3 x 64, Ns = 16, m = 0.005): CGNE on S M with the trained network against plain mixed-precision CGNE
+    and against the untrained (Neumann-initialised) network, every solve to an FP64 true residual of 1e-10.
+
+    Links: U = exp(i eps sum_a lambda^a r^a) with seeded r^a ~ N(0, 1) (the generator's recipe), made on the
+    device by the library's exact SU(3) exponential (hmc_link_update of the unit field with P = 2 eps r,
+    tau = 1): the host generator's batched eigendecompositions take minutes at this volume. Training: for
+    each training configuration in turn, `c4_pairs` seeded Gaussian vectors r_i, `c4_steps` Adam steps on
+    the residual loss |S M r - r|^2 / |r|^2 (Adam's moments carry over from one configuration to the
+    next). Prints one JSON line of its own."""
+    import numpy as np
+    import torch
+    from paper_1710_09621_gb300 import build, inputs
+    from paper_1710_09621_gb300.binding import ODWF, Net, solve_opts
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    dims = tuple(int(v) for v in args.c4_dims.split(","))
+    Lx, Ly, Lz, Lt = dims
+    m = 0.005
+    om = inputs.omega_zolotarev(NS, 0.05, 6.2)
+    lat = ODWF(dims, NS, M0, om)
+    shape5 = (NS, Lt, Lz, Ly, Lx, 4, 3)
+
+    def links(seed):
+        r = np.random.default_rng(seed).standard_normal((4, Lt, Lz, Ly, Lx, 8))
+        P = torch.from_numpy(r).to(dev).mul_(2.0 * EPS)
+        del r
+        U = torch.zeros((4, Lt, Lz, Ly, Lx, 3, 3), dtype=torch.complex128, device=dev)
+        for i in range(3):
+            U[..., i, i] = 1.0
+        lat.link_update(U, P, 1.0)
+        return U
+
+    def gauss5(seed):
+        g = torch.Generator(device=dev)
+        g.manual_seed(seed)
+        return torch.randn(shape5, dtype=torch.complex128, device=dev, generator=g)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return out, time.perf_counter() - t0
+
+    net = neu = None
+    t_start = time.perf_counter()
+    train_log = []
+    for c in range(args.c4_train):
+        U = links(inputs.seed_for(5, c))
+        lat.set_gauge(U)
+        del U
+        if net is None:  # a network needs the handle's gauge field; it follows later set_gauge calls
+            net = Net(lat, channels=2)
+            net.set_loss("residual")
+            neu = Net(lat, channels=2)
+        rs = [gauss5(inputs.seed_for(5, 1000 + args.c4_pairs * c + i)) for i in range(args.c4_pairs)]
+        net.set_pairs(rs, m, m)
+        del rs
+        losses, t_tr = timed(lambda: net.train(args.c4_steps, args.lr))
+        train_log.append({"config": c, "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
+                          "seconds": t_tr})
+    t_train = time.perf_counter() - t_start
+    opts_l = solve_opts(tol=TOL, prec="single", delta=1e-3)
+    opts_p = solve_opts(tol=TOL, prec="single", delta=0.01)
+    evals = []
+    for h in range(args.c4_heldout):
+        U = links(inputs.seed_for(5, 500 + h))
+        lat.set_gauge(U)
+        del U
+        b = gauss5(inputs.seed_for(5, 2000 + h))
+        (_, sp), tp = timed(lambda: lat.solve(b, m, m, opts=opts_p))
+        (_, st), tt = timed(lambda: net.solve(b, m, m, opts=opts_l))
+        (_, sn), tn = timed(lambda: neu.solve(b, m, m, opts=opts_l))
+        evals.append({"heldout": h, "plain_cgne": {"seconds": tp, "iters": sp["iters"], "true_residual": sp["true_residual"]},
+                      "trained": {"seconds": tt, "iters": st["iters"], "true_residual": st["true_residual"]},
+                      "neumann": {"seconds": tn, "iters": sn["iters"], "true_residual": sn["true_residual"]}})
+        del b
+    net.close()
+    neu.close()
+    lat.close()
+    mean = lambda k, f: sum(e[k][f] for e in evals) / len(evals)
+    line = {"metric": "learned-preconditioned CGNE time-to-1e-10 on held-out configurations", "value": mean("trained", "seconds"),
+            "unit": "s", "n_gpus": 1, "higher_is_better": False, "dtype": "f32 + bf16 tensor-core network (FP64 residual restarts)",
+            "data": "synthetic",
+            "config": {"workload": f"{Lx}^3x{Lt} Ns=16 optimal DWF (Zolotarev omega on [0.05,6.2]), m0=1.3, m=0.005, links eps=0.3, "
+                                   f"network trained on {args.c4_train} seeded configurations, evaluated on {args.c4_heldout} held-out ones",
+                       "dims": list(dims), "Ns": NS, "mass": m, "tol": TOL},
+            "plain_cgne_seconds": mean("plain_cgne", "seconds"), "neumann_seconds": mean("neumann", "seconds"),
+            "iters": {"trained": mean("trained", "iters"), "neumann": mean("neumann", "iters"),
+                      "plain_cgne": mean("plain_cgne", "iters")},
+            "training": {"configs": args.c4_train, "pairs_per_config": args.c4_pairs, "steps_per_config": args.c4_steps,
+                         "lr": args.lr, "loss": "residual", "seconds": t_train,
+                         "loss_first": train_log[0]["loss_first"], "loss_last": train_log[-1]["loss_last"],
+                         "per_config": train_log},
+            "heldout": evals}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -476,9 +585,19 @@ def main():
     ap.add_argument("--dims", default=None, help="override lattice, e.g. 16,16,16,16 (profiling only)")
     ap.add_argument("--beta", type=float, default=6.2, help="Wilson plaquette coupling of the MD sections")
     ap.add_argument("--no-hmc", action="store_true", help="skip the HMC trajectory section")
+    ap.add_argument("--config4", action="store_true",
+                    help="instead of the default workload: the network trained across seeded configurations and "
+                         "evaluated on held-out ones (32^3 x 64, m = 0.005)")
+    ap.add_argument("--c4-dims", default="32,32,32,64")
+    ap.add_argument("--c4-train", type=int, default=20, help="training configurations")
+    ap.add_argument("--c4-heldout", type=int, default=2, help="held-out evaluation configurations")
+    ap.add_argument("--c4-pairs", type=int, default=2, help="training vectors per configuration")
+    ap.add_argument("--c4-steps", type=int, default=10, help="Adam steps per configuration")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config4:
+        return config4(args)
 
     global DIMS
     if args.delta is None:

@@ -380,8 +380,8 @@ class ODWF:
 
     def autotune(self, prec="single", stream=None):
         """Pick the fastest launch choice of each fused CGNE kernel; returns the timing report."""
-        buf = ctypes.create_string_buffer(8192)
-        self._check(self.lib.odwf_autotune(self.h, _PREC[prec], buf, 8192, _stream_ptr(stream)))
+        buf = ctypes.create_string_buffer(1 << 16)
+        self._check(self.lib.odwf_autotune(self.h, _PREC[prec], buf, 1 << 16, _stream_ptr(stream)))
         return buf.value.decode()
 
     def set_preconditioner(self, net):

@@ -21,7 +21,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libodwf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "eofa.cu", "solver.cpp", "api.cpp", "noalloc.cu", "learned.cu", "hmc.cu"]
+SOURCES = ["kernels.cu", "eofa.cu", "solver.cpp", "api.cpp", "noalloc.cu", "learned.cu", "hmc.cu", "hop_pair.cu"]
 
 
 def nvcc() -> str:
@@ -80,6 +80,9 @@ def build(force: bool = False) -> str:
     """Compile csrc/*.cu and csrc/*.cpp into libodwf.so; returns the library path."""
     if not force and not _stale():
         return LIB
+    # the hash of the sources as they are when the compile starts: a source edited while it runs
+    # leaves the library stale for the next call
+    digest = source_hash()
     os.makedirs(BUILD, exist_ok=True)
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(_compile, SOURCES))
@@ -90,7 +93,7 @@ def build(force: bool = False) -> str:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
     with open(STAMP, "w") as fh:
-        fh.write(source_hash() + "\n")
+        fh.write(digest + "\n")
     return LIB
 
 

@@ -326,10 +326,11 @@ int odwf_create(odwf_t** out, const int dims[4], int Ns, double m0, const double
     }
     // geometry tables (host-built, uploaded once)
     const int Lx = dims[0], Ly = dims[1], Lz = dims[2], Lt = dims[3];
-    std::vector<int> lexof[2], cbof(V), nbr[2];
+    std::vector<int> lexof[2], cbof(V), nbr[2], nbrs[2];
     for (int p = 0; p < 2; ++p) {
         lexof[p].resize(h->Vh);
         nbr[p].resize((size_t)h->Vh * 8);
+        nbrs[p].resize((size_t)h->Vh * 8);
     }
     // Checkerboard order: the lattice is tiled by 2^4 blocks (all extents are even); block b holds
     // the checkerboard indices 8b .. 8b+7 of each parity, lexicographic inside the block. A CTA of
@@ -358,6 +359,11 @@ int odwf_create(odwf_t** out, const int dims[4], int Ns, double m0, const double
                 const int lb = b[0] + Lx * (b[1] + Ly * (b[2] + Lz * b[3]));
                 nbr[p][(size_t)cb * 8 + mu] = cbof[lf];
                 nbr[p][(size_t)cb * 8 + 4 + mu] = cbof[lb];
+                // signed table of the two-slice kernels: ~index where the link crosses the antiperiodic
+                // t boundary (U_t(x) at x_t = Lt - 1, U_t(x - t)^dag at x_t = 0)
+                const bool fneg = mu == 3 && c[3] == Lt - 1, bneg = mu == 3 && c[3] == 0;
+                nbrs[p][(size_t)cb * 8 + mu] = fneg ? ~cbof[lf] : cbof[lf];
+                nbrs[p][(size_t)cb * 8 + 4 + mu] = bneg ? ~cbof[lb] : cbof[lb];
             }
         }
     int rc = ODWF_OK;
@@ -366,6 +372,9 @@ int odwf_create(odwf_t** out, const int dims[4], int Ns, double m0, const double
         if (!rc) rc = alloc(h, (void**)&h->nbr[p], sizeof(int) * 8 * (size_t)h->Vh);
         if (!rc) rc = alloc(h, (void**)&h->U64[p], sizeof(double) * 8 * 18 * (size_t)h->Vh);
         if (!rc) rc = alloc(h, (void**)&h->U32[p], sizeof(float) * 8 * 20 * (size_t)h->Vh);
+        if (!rc) rc = alloc(h, (void**)&h->U12[p], sizeof(float) * 8 * 12 * (size_t)h->Vh);
+        if (!rc) rc = alloc(h, (void**)&h->nbrs[p], sizeof(int) * 8 * (size_t)h->Vh);
+        if (!rc) rc = cuda_check(h, cudaMemcpy(h->nbrs[p], nbrs[p].data(), sizeof(int) * 8 * (size_t)h->Vh, cudaMemcpyHostToDevice), "upload nbrs");
         if (!rc) rc = cuda_check(h, cudaMemcpy(h->lexof[p], lexof[p].data(), sizeof(int) * h->Vh, cudaMemcpyHostToDevice), "upload lexof");
         if (!rc) rc = cuda_check(h, cudaMemcpy(h->nbr[p], nbr[p].data(), sizeof(int) * 8 * (size_t)h->Vh, cudaMemcpyHostToDevice), "upload nbr");
     }
@@ -373,10 +382,13 @@ int odwf_create(odwf_t** out, const int dims[4], int Ns, double m0, const double
     if (!rc) rc = alloc(h, (void**)&h->partials, sizeof(double) * h->partials_n);
     if (!rc) rc = alloc(h, (void**)&h->state, sizeof(CGState));
     if (!rc) rc = alloc(h, (void**)&h->fault, sizeof(unsigned int));
+    if (!rc) rc = alloc(h, (void**)&h->u12_dev, sizeof(unsigned int));
+    if (!rc) rc = cuda_check(h, cudaMallocHost((void**)&h->u12_dev_host, sizeof(unsigned int)), "cudaMallocHost link check");
     if (!rc) rc = cuda_check(h, cudaMemset(h->fault, 0, sizeof(unsigned int)), "memset fault");
     if (const char* e = std::getenv("ODWF_STAGED")) h->staged = (e[0] == '1') ? 1 : 0;
     if (const char* e = std::getenv("ODWF_TEST_WAIT_CYCLES")) h->wait_cycles = std::atoll(e);
     if (const char* e = std::getenv("ODWF_DENSE_S")) h->dense_s = (e[0] == '1');
+    if (const char* e = std::getenv("ODWF_PAIR")) h->pair = (e[0] >= '0' && e[0] <= '3') ? e[0] - '0' : -1;
     if (!rc) rc = cuda_check(h, cudaMallocHost((void**)&h->fault_host, sizeof(unsigned int)), "cudaMallocHost fault");
     if (!rc) *h->fault_host = 0u;
     if (!rc) rc = cuda_check(h, cudaMemset(h->state, 0, sizeof(CGState)), "memset state");
@@ -397,7 +409,11 @@ int odwf_destroy(odwf_t* h) {
         cudaFree(h->lexof[p]);
         cudaFree(h->U64[p]);
         cudaFree(h->U32[p]);
+        cudaFree(h->U12[p]);
+        cudaFree(h->nbrs[p]);
     }
+    cudaFree(h->u12_dev);
+    if (h->u12_dev_host) cudaFreeHost(h->u12_dev_host);
     for (auto& kv : h->coefs) cudaFree(kv.second.dev);
     for (auto& r : h->prof_recs) {
         cudaEventDestroy(r.a);
@@ -691,14 +707,17 @@ extern "C" int odwf_autotune(odwf_t* h, int prec, char* report, int report_len, 
     std::vector<std::string> log;
     rc = autotune_storage(h, stg, c, (cudaStream_t)stream, log);
     if (report && report_len > 0) {
-        std::string all;
-        for (auto& l : log) all += l + "\n";
+        // the chosen launches first: a short buffer keeps them and loses only timing lines
+        std::string all, timings;
+        for (auto& l : log) timings += l + "\n";
         for (auto& kv : h->tune) {
             char buf[128];
-            std::snprintf(buf, sizeof buf, "chosen key %d: grid-mode %d staged %d tile x%d %s\n", kv.first,
-                          kv.second.mode, kv.second.staged, kv.second.spbm, kv.second.dense ? "dense" : "structured");
+            std::snprintf(buf, sizeof buf, "chosen key %d: grid-mode %d staged %d tile x%d %s%s\n", kv.first,
+                          kv.second.mode, kv.second.staged, kv.second.spbm, kv.second.dense ? "dense" : "structured",
+                          kv.second.pair == 1 ? " two-slice" : (kv.second.pair >= 2 ? " two-slice bulk" : ""));
             all += buf;
         }
+        all += timings;
         std::strncpy(report, all.c_str(), report_len - 1);
         report[report_len - 1] = 0;
     }
@@ -707,7 +726,8 @@ extern "C" int odwf_autotune(odwf_t* h, int prec, char* report, int report_len, 
 
 // ---- persisted autotuner choices ---------------------------------------------------------------
 // One text line per (device, lattice, Ns, precision):
-//   <device name>|<Lx>x<Ly>x<Lz>x<Lt>|<Ns>|<prec>|<kernel key>:<grid mode>:<staged>:<tile>,...
+//   <device name>|<Lx>x<Ly>x<Lz>x<Lt>|<Ns>|<prec>|<kernel key>:<grid mode>:<staged>:<tile>:<dense>:<two-slice>,...
+// (entries written before the last two fields existed read them as 0)
 namespace {
 
 std::string tune_key(const odwf_s* h, int prec) {
@@ -753,10 +773,11 @@ extern "C" int odwf_autotune_cache(odwf_t* h, int prec, const char* path, int* h
                 if (end == std::string::npos) end = found.size();
                 int k = 0;
                 TuneChoice tc;
-                const int nf = std::sscanf(found.substr(pos, end - pos).c_str(), "%d:%d:%d:%d:%d", &k, &tc.mode, &tc.staged,
-                                           &tc.spbm, &tc.dense);
+                const int nf = std::sscanf(found.substr(pos, end - pos).c_str(), "%d:%d:%d:%d:%d:%d", &k, &tc.mode, &tc.staged,
+                                           &tc.spbm, &tc.dense, &tc.pair);
                 if (nf < 4 || tc.mode < 0 || tc.mode > 3 || tc.staged < 0 || tc.staged > 1 || tc.spbm < 1 ||
-                    tc.spbm > 2 || tc.dense < 0 || tc.dense > 1 || (k / 100000) % 10 != stg) {
+                    tc.spbm > 2 || tc.dense < 0 || tc.dense > 1 || tc.pair < 0 || tc.pair > 3 ||
+                    (k / 100000) % 10 != stg) {
                     bad = true;
                     break;
                 }
@@ -777,8 +798,8 @@ extern "C" int odwf_autotune_cache(odwf_t* h, int prec, const char* path, int* h
     for (auto& kv : h->tune) {
         if ((kv.first / 100000) % 10 != stg) continue;
         char buf[64];
-        std::snprintf(buf, sizeof buf, "%s%d:%d:%d:%d:%d", first ? "" : ",", kv.first, kv.second.mode, kv.second.staged,
-                      kv.second.spbm, kv.second.dense);
+        std::snprintf(buf, sizeof buf, "%s%d:%d:%d:%d:%d:%d", first ? "" : ",", kv.first, kv.second.mode,
+                      kv.second.staged, kv.second.spbm, kv.second.dense, kv.second.pair);
         entry += buf;
         first = false;
     }

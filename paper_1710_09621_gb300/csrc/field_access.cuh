@@ -138,6 +138,33 @@ struct Links<ST_FLOAT> {
 template <>
 struct Links<ST_HALF> : Links<ST_FLOAT> {};
 
+// Two-row links (FP32 [Vh][8][12]): the first two rows of an SU(3) matrix V, whose third row is the
+// complex conjugate of the cross product of the first two (V^{-1} = V^dag and det V = 1 make row 2 the
+// conjugated cofactors of rows 0 and 1). link12_complete fills u[12..17] = conj(row 0 x row 1) from
+// u[0..11]; link12_load reads rows 0 and 1 of link (cb, dir) and completes them.
+__device__ __forceinline__ void link12_complete(float u[18]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int i = (k + 1) % 3, j = (k + 2) % 3;
+        const float ar = u[2 * i], ai = u[2 * i + 1], br = u[6 + 2 * j], bi = u[6 + 2 * j + 1];
+        const float cr = u[2 * j], ci = u[2 * j + 1], dr = u[6 + 2 * i], di = u[6 + 2 * i + 1];
+        // (r0 x r1)_k = r0_i r1_j - r0_j r1_i
+        const float re = fmaf(ar, br, -ai * bi) - fmaf(cr, dr, -ci * di);
+        const float im = fmaf(ar, bi, ai * br) - fmaf(cr, di, ci * dr);
+        u[12 + 2 * k] = re;
+        u[13 + 2 * k] = -im;
+    }
+}
+
+__device__ __forceinline__ void link12_load(const float* base, int cb, int dir, float u[18]) {
+    const float4* p = reinterpret_cast<const float4*>(base) + ((size_t)cb * 8 + dir) * 3;
+    const float4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+    u[0] = a.x, u[1] = a.y, u[2] = a.z, u[3] = a.w;
+    u[4] = b.x, u[5] = b.y, u[6] = b.z, u[7] = b.w;
+    u[8] = c.x, u[9] = c.y, u[10] = c.z, u[11] = c.w;
+    link12_complete(u);
+}
+
 // Rows of 24 reals (one (site, s) spinor) in shared memory, moved as 16-byte vectors. Every row
 // start is 16-byte aligned: rows are 96 (FP32) or 192 (FP64) bytes and the staging buffers start at
 // 16-byte aligned offsets.

@@ -14,104 +14,14 @@
 // with C_mu = B_mu^dag unitary: (1 -/+ gamma_mu) psi = [h; -/+ C h], h = psi_up -/+ B psi_dn, so each
 // direction multiplies one 2-spin half spinor by U.
 #include <cstdio>
+#include <cstring>
 #include <type_traits>
 
-#include "field_access.cuh"
+#include "hop_common.cuh"
 
 namespace odwf {
 
 int spb_for(int Ns);
-
-// ---- complex helpers on interleaved real arrays ------------------------------------------------
-// spinor index of (spin, color) real part: (spin * 3 + color) * 2
-
-template <typename R>
-__device__ __forceinline__ void cadd(R* o, const R* a) { o[0] += a[0]; o[1] += a[1]; }
-
-// h = psi_up + SIGN * B_mu psi_dn  (SIGN = -1 for 1 - gamma_mu, +1 for 1 + gamma_mu)
-template <int MU, int SIGN, typename R>
-__device__ __forceinline__ void project(const R* p, R* h) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const R* u0 = p + (0 * 3 + c) * 2;
-        const R* u1 = p + (1 * 3 + c) * 2;
-        const R* d0 = p + (2 * 3 + c) * 2;
-        const R* d1 = p + (3 * 3 + c) * 2;
-        R* h0 = h + (0 * 3 + c) * 2;
-        R* h1 = h + (1 * 3 + c) * 2;
-        if (MU == 0) {  // B = -i sigma_1: (B d)_0 = -i d1, (B d)_1 = -i d0; -i z = (z.im, -z.re)
-            h0[0] = u0[0] + SIGN * d1[1]; h0[1] = u0[1] - SIGN * d1[0];
-            h1[0] = u1[0] + SIGN * d0[1]; h1[1] = u1[1] - SIGN * d0[0];
-        } else if (MU == 1) {  // B = -i sigma_2 = [[0,-1],[1,0]]: (B d)_0 = -d1, (B d)_1 = d0
-            h0[0] = u0[0] - SIGN * d1[0]; h0[1] = u0[1] - SIGN * d1[1];
-            h1[0] = u1[0] + SIGN * d0[0]; h1[1] = u1[1] + SIGN * d0[1];
-        } else if (MU == 2) {  // B = -i sigma_3: (B d)_0 = -i d0, (B d)_1 = +i d1; i z = (-z.im, z.re)
-            h0[0] = u0[0] + SIGN * d0[1]; h0[1] = u0[1] - SIGN * d0[0];
-            h1[0] = u1[0] - SIGN * d1[1]; h1[1] = u1[1] + SIGN * d1[0];
-        } else {  // B = 1
-            h0[0] = u0[0] + SIGN * d0[0]; h0[1] = u0[1] + SIGN * d0[1];
-            h1[0] = u1[0] + SIGN * d1[0]; h1[1] = u1[1] + SIGN * d1[1];
-        }
-    }
-}
-
-// v_up += w ; v_dn += SIGN * C_mu w   (SIGN = -1 for 1 - gamma_mu, +1 for 1 + gamma_mu)
-template <int MU, int SIGN, typename R>
-__device__ __forceinline__ void reconstruct(R* v, const R* w) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const R* w0 = w + (0 * 3 + c) * 2;
-        const R* w1 = w + (1 * 3 + c) * 2;
-        R* v0 = v + (0 * 3 + c) * 2;
-        R* v1 = v + (1 * 3 + c) * 2;
-        R* v2 = v + (2 * 3 + c) * 2;
-        R* v3 = v + (3 * 3 + c) * 2;
-        cadd(v0, w0);
-        cadd(v1, w1);
-        if (MU == 0) {  // C = i sigma_1: (C w)_0 = i w1, (C w)_1 = i w0
-            v2[0] += SIGN * (-w1[1]); v2[1] += SIGN * w1[0];
-            v3[0] += SIGN * (-w0[1]); v3[1] += SIGN * w0[0];
-        } else if (MU == 1) {  // C = i sigma_2 = [[0,1],[-1,0]]: (C w)_0 = w1, (C w)_1 = -w0
-            v2[0] += SIGN * w1[0]; v2[1] += SIGN * w1[1];
-            v3[0] -= SIGN * w0[0]; v3[1] -= SIGN * w0[1];
-        } else if (MU == 2) {  // C = i sigma_3: (C w)_0 = i w0, (C w)_1 = -i w1
-            v2[0] += SIGN * (-w0[1]); v2[1] += SIGN * w0[0];
-            v3[0] += SIGN * w1[1]; v3[1] += SIGN * (-w1[0]);
-        } else {  // C = 1
-            v2[0] += SIGN * w0[0]; v2[1] += SIGN * w0[1];
-            v3[0] += SIGN * w1[0]; v3[1] += SIGN * w1[1];
-        }
-    }
-}
-
-// w[spin a] = U h[spin a] for the two spins of a half spinor
-template <typename R>
-__device__ __forceinline__ void su3_mul_half(const R* u, const R* h, R* w) {
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            R re = 0, im = 0;
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const R ur = u[(i * 3 + j) * 2], ui = u[(i * 3 + j) * 2 + 1];
-                const R hr = h[(a * 3 + j) * 2], hi = h[(a * 3 + j) * 2 + 1];
-                re = fma(ur, hr, re);
-                re = fma(-ui, hi, re);
-                im = fma(ur, hi, im);
-                im = fma(ui, hr, im);
-            }
-            w[(a * 3 + i) * 2] = re;
-            w[(a * 3 + i) * 2 + 1] = im;
-        }
-    }
-}
-
-template <typename R>
-__device__ __forceinline__ void g5_flip(R* v) {
-#pragma unroll
-    for (int k = 12; k < 24; ++k) v[k] = -v[k];
-}
 
 template <int ST, int MU>
 __device__ __forceinline__ void hop_dir(const HopArgs& a, const int* n, int cb, int s,
@@ -134,133 +44,6 @@ __device__ __forceinline__ void hop_dir(const HopArgs& a, const int* n, int cb, 
     reconstruct<MU, +1>(v, w);
 }
 
-__device__ __forceinline__ double block_reduce_sum(double v, double* wsum) {
-    const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
-    const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (blockDim.x * blockDim.y + 31) >> 5;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    __syncthreads();
-    if (lane == 0) wsum[warp] = v;
-    __syncthreads();
-    double tot = 0.0;
-    if (threadIdx.x == 0 && threadIdx.y == 0)
-        for (int w = 0; w < nwarps; ++w) tot += wsum[w];
-    return tot;  // valid in thread (0,0)
-}
-
-// Deterministic grid reduction: every block writes its partial; the last block to finish sums
-// the partials in index order and runs the epilogue's scalar update.
-template <int EPI>
-__device__ void grid_finalize(const HopArgs& a, double part) {
-    __shared__ double wsum[32];
-    __shared__ int is_last;
-    const double bsum = block_reduce_sum(part, wsum);
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        a.partials[blockIdx.x] = bsum;
-        __threadfence();
-        const unsigned t = atomicAdd(&a.state->ticket, 1u);
-        is_last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    const int nth = blockDim.x * blockDim.y;
-    double acc = 0.0;
-    for (int i = tid; i < (int)gridDim.x; i += nth) acc += ((volatile double*)a.partials)[i];
-    const double tot = block_reduce_sum(acc, wsum);
-    if (tid == 0) {
-        CGState* st = a.state;
-        st->ticket = 0;
-        if (EPI == EPI_CG_A) {
-            const double rr_new = tot;
-            st->iter += 1;
-            if (!isfinite(rr_new)) {
-                st->flag = FLAG_BREAKDOWN;
-            } else {
-                st->beta = rr_new / st->rr;
-                st->rr = rr_new;
-                if (rr_new > st->rr_max) st->rr_max = rr_new;
-                if (rr_new <= st->tol2) st->flag = FLAG_CONVERGED;
-                else if (st->delta2 > 0.0 && rr_new < st->delta2 * st->rr_max) st->flag = FLAG_UPDATE;
-                else if (st->iter >= st->maxiter) st->flag = FLAG_MAXITER;
-            }
-        } else if (EPI == EPI_CG_B) {
-            st->pp = tot;
-            if (!(tot > 0.0) || !isfinite(tot)) st->flag = FLAG_BREAKDOWN;
-            else st->alpha = st->rr / tot;
-        } else {
-            st->result[a.slot] = tot;
-        }
-    }
-}
-
-// Generic kernel for one output parity:
-//   v = c_hop * H(in)                              (HOP; in gets gamma_5 if G5_HOP_IN)
-//   v += a_own * own                               (OWN && !MIXOWN; own gets gamma_5 if G5_OWN_IN)
-//   v = Mhop v                                     (MIXHOP)
-//   v += Mown own                                  (MIXOWN)
-//   v = gamma_5 v                                  (G5_OUT)
-//   epilogue EPI
-// Epilogue of the fused kernels for one (site, s): store, residual, or the CGNE updates; adds the
-// thread's contribution to the block reduction in `part`.
-template <int ST, int EPI>
-__device__ __forceinline__ void epilogue(const HopArgs& a, int cb, int s, typename Store<ST>::R* v,
-                                         const typename Store<ST>::R* ow, double alpha, double beta, double& part) {
-    using S = Store<ST>;
-    using R = typename S::R;
-    const int Ns = a.Ns;
-    if (EPI == EPI_STORE || EPI == EPI_STORE_NORM) {
-        S::store(a.out, a.out_scale, (size_t)cb, s, Ns, v);
-        if (EPI == EPI_STORE_NORM) {
-            R t = 0;
-#pragma unroll
-            for (int k = 0; k < 24; ++k) t = fma(v[k], v[k], t);
-            part += (double)t;
-        }
-    } else if (EPI == EPI_RESID) {
-        R b[24];
-        S::load(a.x, a.x_scale, (size_t)cb, s, Ns, b);
-        R t = 0;
-#pragma unroll
-        for (int k = 0; k < 24; ++k) {
-            b[k] -= v[k];
-            t = fma(b[k], b[k], t);
-        }
-        S::store(a.out, a.out_scale, (size_t)cb, s, Ns, b);
-        part += (double)t;
-    } else if (EPI == EPI_CG_A) {
-        // x += alpha * own (own = p, without gamma_5), r -= alpha * v
-        R x[24], r[24];
-        S::load(a.x, a.x_scale, (size_t)cb, s, Ns, x);
-        S::load(a.r, a.r_scale, (size_t)cb, s, Ns, r);
-        const R al = (R)alpha;
-        R t = 0;
-#pragma unroll
-        for (int k = 0; k < 24; ++k) {
-            x[k] = fma(al, ow[k], x[k]);
-            r[k] = fma(-al, v[k], r[k]);
-            t = fma(r[k], r[k], t);
-        }
-        S::store(a.x, a.x_scale, (size_t)cb, s, Ns, x);
-        S::store(a.r, a.r_scale, (size_t)cb, s, Ns, r);
-        part += (double)t;
-    } else if (EPI == EPI_CG_B) {
-        // p = v + beta * p
-        R p[24];
-        S::load(a.r, a.r_scale, (size_t)cb, s, Ns, p);
-        const R be = (R)beta;
-        R t = 0;
-#pragma unroll
-        for (int k = 0; k < 24; ++k) {
-            p[k] = fma(be, p[k], v[k]);
-            t = fma(p[k], p[k], t);
-        }
-        S::store(a.r, a.r_scale, (size_t)cb, s, Ns, p);
-        part += (double)t;
-    }
-}
 
 // Barrier over the threads that share staged rows: the whole CTA, or just the warp when every site
 // lies inside one warp (WS: Ns divides 32, so a site's Ns threads are consecutive lanes of one warp
@@ -277,6 +60,13 @@ constexpr bool kLeanK1 = true;
 template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN>
 constexpr bool kLeanHop = kLeanK1 && ST == ST_FLOAT && HOP && MIXHOP && !OWN && !MIXOWN;
 
+// Generic kernel for one output parity:
+//   v = c_hop * H(in)                              (HOP; in gets gamma_5 if G5_HOP_IN)
+//   v += a_own * own                               (OWN && !MIXOWN; own gets gamma_5 if G5_OWN_IN)
+//   v = Mhop v                                     (MIXHOP)
+//   v += Mown own                                  (MIXOWN)
+//   v = gamma_5 v                                  (G5_OUT)
+//   epilogue EPI
 // SN > 0 (= kStructNs = Ns): the fifth-dimension product is the structured O(Ns) recurrence of
 // a.sop (s_struct_col) instead of the dense Ns x Ns matrix.
 template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI, bool WS, int SN>
@@ -444,60 +234,6 @@ __device__ __forceinline__ const HopArgs& stage_args(const HopArgs* __restrict__
 // outside it (fetched individually through the neighbour table). Shared memory per CTA:
 //   slots [k*8 inside + 4*spb outside][NCH][Ns] 16-byte chunks (+ FP16 scales), the CTA's links
 //   [spb][8][20] floats, and the fifth-dimension matrices; the s-mixing buffer aliases the slots.
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Wait for phase `parity` for at most ~1 s of SM clock (limit <= 0), or for at most `limit` cycles
-// polled with the non-blocking test (a caller-set limit, which tests use to make the wait run out);
-// false on time-out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit = 0) {
-    const long long t0 = clock64();
-    if (limit > 0) {
-        while (!mbar_test_wait(bar, parity))
-            if (clock64() - t0 > limit) return false;
-        return true;
-    }
-    while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > 2000000000LL) return false;
-    }
-    return true;
-}
-
 template <int ST>
 struct StagedGeom {
     static constexpr int NCH = Store<ST>::NCH;
@@ -761,16 +497,16 @@ __global__ void __launch_bounds__(256, 4) k_hop_lean(HopArgs a) {
 // Several independent systems in one launch: blockIdx.y selects the system's arguments (its own
 // fields, lattice tables, solver state and reduction buffer); blockIdx.x strides over its sites.
 // Systems that are converged or waiting for a host-side update return at once.
-template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI, bool WS>
+template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI, bool WS, int SN = 0>
 __global__ void __launch_bounds__(256) k_hop_multi(const HopArgs* __restrict__ args) {
     __shared__ HopArgs sa;
-    hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS, 0>(stage_args(args, &sa));
+    hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS, SN>(stage_args(args, &sa));
 }
 
-template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI, bool WS>
+template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI, bool WS, int SN = 0>
 __global__ void __launch_bounds__(256, 4) k_hop_multi_lean(const HopArgs* __restrict__ args) {
     __shared__ HopArgs sa;
-    hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS, 0>(stage_args(args, &sa));
+    hop_body<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS, SN>(stage_args(args, &sa));
 }
 
 // the per-thread-gather kernel of a variant, single system and several systems; WS (Ns divides
@@ -781,10 +517,10 @@ constexpr auto hop_kernel() {
     if constexpr (kLeanHop<ST, HOP, MIXHOP, OWN, MIXOWN>) return k_hop_lean<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS, SN>;
     else return k_hop<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS, SN>;
 }
-template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI, bool WS>
+template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI, bool WS, int SN = 0>
 constexpr auto hop_multi_kernel() {
-    if constexpr (kLeanHop<ST, HOP, MIXHOP, OWN, MIXOWN>) return k_hop_multi_lean<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS>;
-    else return k_hop_multi<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS>;
+    if constexpr (kLeanHop<ST, HOP, MIXHOP, OWN, MIXOWN>) return k_hop_multi_lean<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS, SN>;
+    else return k_hop_multi<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, WS, SN>;
 }
 
 static bool warp_sites(int Ns) { return 32 % Ns == 0; }
@@ -806,6 +542,8 @@ int spb_for(int Ns) {
 void hop_fill(odwf_s* h, int storage, int parity, HopArgs& a, bool reduces) {
     a.links = (storage == ST_DOUBLE) ? (const void*)h->U64[parity] : (const void*)h->U32[parity];
     a.nbr = h->nbr[parity];
+    a.links12 = h->U12[parity];
+    a.nbrs = h->nbrs[parity];
     a.Vh = h->Vh;
     a.Ns = h->Ns;
     a.parity = parity;
@@ -828,7 +566,7 @@ static bool staged_ok(const odwf_s* h, int st) { return h->staged && staged_geom
 
 // Grid of a fused kernel: mode 0 one resident wave (SMs x occupancy), 1 one CTA per site group,
 // 2 / 3 two / four resident waves; reducing kernels are capped by the partial-sum buffer.
-static int grid_for_mode(const odwf_s* h, int mode, int occ, int groups, bool reduces) {
+int grid_for_mode(const odwf_s* h, int mode, int occ, int groups, bool reduces) {
     long g;
     switch (mode) {
         case 1: g = groups; break;
@@ -845,7 +583,8 @@ template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
 struct KernelPick {
     static constexpr bool CAN_STAGE = HOP && ST != ST_DOUBLE;
     static constexpr bool CAN_STRUCT = MIXHOP || MIXOWN;
-    // kind: 0 plain single, 1 plain multi, 2 staged single, 3 staged multi, 4 structured single
+    // kind: 0 plain single, 1 plain multi, 2 staged single, 3 staged multi, 4 structured single,
+    // 5 structured multi
     static const void* fn(int kind, bool ws) {
         if constexpr (CAN_STAGE) {
             if (kind == 2) return (const void*)k_hop_staged<ST, MIXHOP, OWN, MIXOWN, EPI>;
@@ -853,6 +592,7 @@ struct KernelPick {
         }
         if constexpr (CAN_STRUCT) {
             if (kind == 4) return (const void*)hop_kernel<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, true, kStructNs>();
+            if (kind == 5) return (const void*)hop_multi_kernel<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, true, kStructNs>();
         }
         if (ws)
             return kind == 1 ? (const void*)hop_multi_kernel<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, true>()
@@ -874,10 +614,11 @@ static int occupancy(odwf_s* h, int kind, size_t* smem_out, int spb = 0) {
     if constexpr (ST != ST_DOUBLE) {
         if (kind == 2 || kind == 3) smem = staged_smem<ST>(Ns, spb, MIXHOP, MIXOWN);
     }
-    if (kind == 4) smem = sizeof(R) * (size_t)spb * kSSite<R>;
+    if (kind == 4 || kind == 5) smem = sizeof(R) * (size_t)spb * kSSite<R>;
     *smem_out = smem;
     static std::map<long, int> occ_cache;  // (kind, Ns, sites per CTA) -> resident CTAs per SM
-    static bool attr_set[5][2] = {{false, false}, {false, false}, {false, false}, {false, false}, {false, false}};
+    static bool attr_set[6][2] = {{false, false}, {false, false}, {false, false},
+                                  {false, false}, {false, false}, {false, false}};
     const bool ws = warp_sites(Ns);
     const void* fn = KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::fn(kind, ws);
     if (!attr_set[kind][ws]) {
@@ -894,10 +635,13 @@ static int occupancy(odwf_s* h, int kind, size_t* smem_out, int spb = 0) {
 }
 
 template <int ST, bool HOP, bool MIXHOP, bool OWN, bool MIXOWN, int EPI>
-static int launch_multi_one(odwf_s* h, const HopArgs* dev_args, int n, int max_vh, cudaStream_t st) {
+static int launch_multi_one(odwf_s* h, const HopArgs* dev_args, int n, int max_vh, bool structured, cudaStream_t st) {
     size_t smem = 0;
     const bool stg = KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::CAN_STAGE && staged_ok(h, ST);
-    const int kind = stg ? 3 : 1;
+    // structured fifth-dimension products: every system's arguments carry them (Ns = kStructNs)
+    const bool sn = KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::CAN_STRUCT && !stg && structured &&
+                    h->Ns == kStructNs;
+    const int kind = stg ? 3 : (sn ? 5 : 1);
     const int occ = occupancy<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(h, kind, &smem);
     const int spb = spb_for(h->Ns);
     const int groups = (max_vh + spb - 1) / spb;
@@ -913,6 +657,13 @@ static int launch_multi_one(odwf_s* h, const HopArgs* dev_args, int n, int max_v
             h->staged_used = true;
             k_hop_staged_multi<ST, MIXHOP, OWN, MIXOWN, EPI><<<dim3(gx, n), dim3(h->Ns, spb), smem, st>>>(dev_args);
             return cuda_check(h, cudaGetLastError(), "k_hop_staged_multi launch");
+        }
+    }
+    if constexpr (KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::CAN_STRUCT) {
+        if (sn) {
+            hop_multi_kernel<ST, HOP, MIXHOP, OWN, MIXOWN, EPI, true, kStructNs>()<<<dim3(gx, n), dim3(h->Ns, spb), smem, st>>>(
+                dev_args);
+            return cuda_check(h, cudaGetLastError(), "k_hop_multi launch");
         }
     }
     if (warp_sites(h->Ns))
@@ -942,6 +693,23 @@ static int launch_one(odwf_s* h, int parity, HopArgs a, cudaStream_t st) {
     // the structured fifth-dimension product: single-system per-thread-gather kernels at Ns = kStructNs
     const bool sn = KernelPick<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>::CAN_STRUCT && !stg && Ns == kStructNs &&
                     a.sop != SOP_DENSE && !force_dense;
+    // two slices per thread (hop_pair.cu): ODWF_PAIR=1 wherever it applies, else the tuned choice
+    int pair = 0;
+    int pair_tile = 1;
+    if (sn && HOP && pair_variant(ST, MIXHOP, OWN, MIXOWN, EPI) && pair_applies(h, ST, a) && h->pair != 0) {
+        if (h->pair > 0) pair = h->pair;
+        else if (tuned != h->tune.end()) pair = tuned->second.pair;
+        if (tuned != h->tune.end()) pair_tile = tuned->second.spbm;
+    }
+    if (pair) {
+        hop_fill(h, ST, parity, a, EPI != EPI_STORE);
+        const int pkey = base_key + 500000 + (pair >= 2 && pair_tma_applies(ST, a) ? 1000000 : 0);
+        cudaEvent_t ev = nullptr;
+        if (h->prof) prof_begin(h, pkey, st, &ev);
+        const int rc = launch_hop_pair(h, ST, MIXHOP, OWN, MIXOWN, EPI, a, mode, pair_tile, st, pair);
+        if (h->prof) prof_end(h, pkey, st, ev);
+        return rc;
+    }
     const int occ = occupancy<ST, HOP, MIXHOP, OWN, MIXOWN, EPI>(h, stg ? 2 : (sn ? 4 : 0), &smem, spb);
     const int groups = (h->Vh + spb - 1) / spb;
     const int grid = grid_for_mode(h, mode, occ, groups, EPI != EPI_STORE);
@@ -992,10 +760,10 @@ static int launch_st(odwf_s* h, int parity, bool hop, bool mixhop, bool own, boo
 
 template <int ST>
 static int launch_multi_st(odwf_s* h, bool mixhop, bool own, bool mixown, int epi, const HopArgs* dev_args, int n,
-                           int max_vh, cudaStream_t st) {
+                           int max_vh, bool structured, cudaStream_t st) {
 #define ODWF_MCASE(MH, OW, MO, E)                                                                  \
     if (mixhop == MH && own == OW && mixown == MO && epi == E)                                     \
-        return launch_multi_one<ST, true, MH, OW, MO, E>(h, dev_args, n, max_vh, st);
+        return launch_multi_one<ST, true, MH, OW, MO, E>(h, dev_args, n, max_vh, structured, st);
     ODWF_MCASE(true, false, false, EPI_STORE)
     ODWF_MCASE(false, true, true, EPI_CG_A)
     ODWF_MCASE(false, true, true, EPI_CG_B)
@@ -1004,11 +772,11 @@ static int launch_multi_st(odwf_s* h, bool mixhop, bool own, bool mixown, int ep
 }
 
 int launch_hop_multi(odwf_s* h, int storage, bool mixhop, bool own, bool mixown, int epi, const HopArgs* dev_args,
-                     int n, int max_vh, cudaStream_t st) {
+                     int n, int max_vh, cudaStream_t st, bool structured) {
     switch (storage) {
-        case ST_DOUBLE: return launch_multi_st<ST_DOUBLE>(h, mixhop, own, mixown, epi, dev_args, n, max_vh, st);
-        case ST_FLOAT: return launch_multi_st<ST_FLOAT>(h, mixhop, own, mixown, epi, dev_args, n, max_vh, st);
-        case ST_HALF: return launch_multi_st<ST_HALF>(h, mixhop, own, mixown, epi, dev_args, n, max_vh, st);
+        case ST_DOUBLE: return launch_multi_st<ST_DOUBLE>(h, mixhop, own, mixown, epi, dev_args, n, max_vh, structured, st);
+        case ST_FLOAT: return launch_multi_st<ST_FLOAT>(h, mixhop, own, mixown, epi, dev_args, n, max_vh, structured, st);
+        case ST_HALF: return launch_multi_st<ST_HALF>(h, mixhop, own, mixown, epi, dev_args, n, max_vh, structured, st);
     }
     return set_err(h, ODWF_EINVAL, "bad storage");
 }
@@ -1268,11 +1036,16 @@ int launch_norm2(odwf_s* h, const void* v, int storage, const float* sc, int slo
 // U (ABI): [mu][lex][3][3] complex128. Output per parity p and checkerboard site cb:
 //   dir mu     : U_mu(x), times -1 when mu = t and x_t = Lt - 1 (antiperiodic fermion boundary)
 //   dir 4 + mu : U_mu(x - mu)^dag, times -1 when mu = t and x_t = 0
+// Also written: U12 (two-slice kernels), rows 0 and 1 of the link without the boundary sign, and in
+// *dev the largest deviation |row 2 - conj(row 0 x row 1)| over all links (as float bits; the
+// two-row links stand for the links only when it is at rounding level).
 __global__ void k_gauge(const double2* __restrict__ U, double* __restrict__ U64e, double* __restrict__ U64o,
-                        float* __restrict__ U32e, float* __restrict__ U32o, const int* __restrict__ lex_e,
+                        float* __restrict__ U32e, float* __restrict__ U32o, float* __restrict__ U12e,
+                        float* __restrict__ U12o, unsigned int* __restrict__ dev, const int* __restrict__ lex_e,
                         const int* __restrict__ lex_o, int Lx, int Ly, int Lz, int Lt, int Vh) {
     const int V = 2 * Vh;
     const int total = 2 * Vh * 8;
+    float dmax = 0.f;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
         const int dir = i % 8;
         const int rest = i / 8;
@@ -1314,16 +1087,45 @@ __global__ void k_gauge(const double2* __restrict__ U, double* __restrict__ U64e
         }
         d32[18] = 0.f;
         d32[19] = 0.f;
+        // the unsigned link sg m: its first two rows, and how far its third row is from conj(row 0 x row 1)
+        const double sg = (mu == 3 && c[3] == (dir < 4 ? Lt - 1 : 0)) ? -1.0 : 1.0;
+        float* d12 = (par ? U12o : U12e) + ((size_t)cb * 8 + dir) * 12;
+        for (int k = 0; k < 12; ++k) d12[k] = (float)(sg * m[k]);
+        for (int k = 0; k < 3; ++k) {
+            const int a = (k + 1) % 3, b = (k + 2) % 3;
+            const double ar = m[2 * a], ai = m[2 * a + 1], br = m[6 + 2 * b], bi = m[6 + 2 * b + 1];
+            const double cr = m[2 * b], ci = m[2 * b + 1], dr = m[6 + 2 * a], di = m[6 + 2 * a + 1];
+            const double re = (ar * br - ai * bi) - (cr * dr - ci * di);
+            const double im = (ar * bi + ai * br) - (cr * di + ci * dr);
+            // sg^2 = 1: the cross product of the signed rows is that of the unsigned ones
+            const double er = fabs(sg * m[12 + 2 * k] - re), ei = fabs(sg * m[13 + 2 * k] + im);
+            dmax = fmaxf(dmax, (float)fmax(er, ei));
+        }
     }
+    if (!(dmax == dmax)) dmax = 3.0e38f;  // NaN links never qualify
+    unsigned int bits = __float_as_uint(dmax);
+    bits = __reduce_max_sync(0xffffffffu, bits);
+    if ((threadIdx.x & 31) == 0) atomicMax(dev, bits);
 }
 
 int launch_gauge(odwf_s* h, const double* U, cudaStream_t st) {
     const int total = 2 * h->Vh * 8;
     int g = (total + 255) / 256;
     if (g > h->num_sms * 16) g = h->num_sms * 16;
-    k_gauge<<<g, 256, 0, st>>>((const double2*)U, h->U64[0], h->U64[1], h->U32[0], h->U32[1], h->lexof[0],
-                               h->lexof[1], h->L[0], h->L[1], h->L[2], h->L[3], h->Vh);
-    return cuda_check(h, cudaGetLastError(), "k_gauge");
+    int rc = cuda_check(h, cudaMemsetAsync(h->u12_dev, 0, sizeof(unsigned int), st), "memset");
+    if (rc) return rc;
+    k_gauge<<<g, 256, 0, st>>>((const double2*)U, h->U64[0], h->U64[1], h->U32[0], h->U32[1], h->U12[0], h->U12[1],
+                               h->u12_dev, h->lexof[0], h->lexof[1], h->L[0], h->L[1], h->L[2], h->L[3], h->Vh);
+    if ((rc = cuda_check(h, cudaGetLastError(), "k_gauge"))) return rc;
+    // the two-slice kernels take the two-row links only for SU(3) links (to well below FP32 rounding)
+    if ((rc = cuda_check(h, cudaMemcpyAsync(h->u12_dev_host, h->u12_dev, sizeof(unsigned int), cudaMemcpyDeviceToHost, st),
+                         "read link check")))
+        return rc;
+    if ((rc = cuda_check(h, cudaStreamSynchronize(st), "link check sync"))) return rc;
+    float d;
+    std::memcpy(&d, h->u12_dev_host, sizeof d);
+    h->links12_ok = d < 1e-6f;
+    return ODWF_OK;
 }
 
 
@@ -1398,17 +1200,24 @@ int autotune_storage(odwf_s* h, int stg, const SCoef* c, cudaStream_t st, std::v
         float best = 1e30f;
         TuneChoice best_choice{};
         const int max_spbm = spb_for(h->Ns) * 2 * h->Ns <= 256 ? 2 : 1;
-        // the structured and the dense fifth-dimension product where both exist (Ns = kStructNs)
+        // the structured and the dense fifth-dimension product where both exist (Ns = kStructNs), and
+        // the two-slice kernel for the structured one
         const int max_dense = (h->Ns == kStructNs && a.sop != SOP_DENSE) ? 1 : 0;
+        hop_fill(h, stg, v.parity, a, false);
+        int max_pair = (max_dense && h->pair != 0 && pair_variant(stg, v.mixhop, v.own, v.mixown, v.epi) &&
+                        pair_applies(h, stg, a)) ? 1 : 0;
+        if (max_pair && pair_tma_applies(stg, a)) max_pair = 3;  // the bulk-copy forms with 2 and 3 stages
         for (int dense = 0; dense <= max_dense; ++dense)
-        for (int spbm = 1; spbm <= max_spbm; ++spbm)
-        for (int staged = 0; staged <= (can_stage && !dense ? 1 : 0); ++staged)
+        for (int pair = 0; pair <= (dense ? 0 : max_pair); ++pair)
+        for (int spbm = 1; spbm <= (pair >= 2 ? 1 : max_spbm); ++spbm)
+        for (int staged = 0; staged <= (can_stage && !dense && !pair ? 1 : 0); ++staged)
             for (int mode = 0; mode < 4; ++mode) {
                 TuneChoice tc;
                 tc.mode = mode;
                 tc.staged = staged;
                 tc.spbm = spbm;
                 tc.dense = dense;
+                tc.pair = pair;
                 h->tune[base_key] = tc;
                 int rc = fill();
                 if (rc) return set_err(h, rc, "autotune: fill");
@@ -1424,8 +1233,10 @@ int autotune_storage(odwf_s* h, int stg, const SCoef* c, cudaStream_t st, std::v
                 cudaEventElapsedTime(&ms, e0, e1);
                 ms /= reps;
                 char buf[160];
-                std::snprintf(buf, sizeof buf, "%s storage %d %s tile x%d staged %d grid-mode %d: %.1f us", v.name, stg,
-                              dense ? "dense" : "structured", spbm, staged, mode, 1e3 * ms);
+                std::snprintf(buf, sizeof buf, "%s storage %d %s%s tile x%d staged %d grid-mode %d: %.1f us", v.name,
+                              stg, dense ? "dense" : "structured",
+                              pair == 1 ? " two-slice" : (pair == 2 ? " two-slice bulk x2" : (pair == 3 ? " two-slice bulk x3" : "")),
+                              spbm, staged, mode, 1e3 * ms);
                 log.push_back(buf);
                 if (ms < best) {
                     best = ms;

@@ -53,6 +53,9 @@ struct NetLayerArgs {
     const float* links;      // FP32 links of the output parity [Vh][8][20]
     const int* nbr;
     int Vh, Ns;
+    // the fifth-dimension mixing `mix` in its structured form (sop != SOP_DENSE, Ns = kStructNs)
+    int sop;
+    SStruct sc;
 };
 
 __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint32_t* b) {
@@ -68,13 +71,8 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
-// T_d psi at (cb, s): full 4-spinor parallel transport by the stored link of direction d.
-__device__ __forceinline__ void transport4(const float* in, const float* links, const int* nbr, int cb, int s,
-                                           int Ns, int d, float out[24]) {
-    float psi[24], u[18];
-    const int n = __ldg(nbr + (size_t)cb * 8 + d);
-    Store<ST_FLOAT>::load(in, nullptr, (size_t)n, s, Ns, psi);
-    Links<ST_FLOAT>::load(links, cb, d, u);
+// out = U psi for the four spins of psi (U: 3 x 3 complex, row-major re/im)
+__device__ __forceinline__ void transport_apply(const float u[18], const float psi[24], float out[24]) {
 #pragma unroll
     for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
@@ -90,6 +88,16 @@ __device__ __forceinline__ void transport4(const float* in, const float* links, 
             out[(sp * 3 + i) * 2] = re;
             out[(sp * 3 + i) * 2 + 1] = im;
         }
+}
+
+// T_d psi at (cb, s): full 4-spinor parallel transport by the stored link of direction d.
+__device__ __forceinline__ void transport4(const float* in, const float* links, const int* nbr, int cb, int s,
+                                           int Ns, int d, float out[24]) {
+    float psi[24], u[18];
+    const int n = __ldg(nbr + (size_t)cb * 8 + d);
+    Store<ST_FLOAT>::load(in, nullptr, (size_t)n, s, Ns, psi);
+    Links<ST_FLOAT>::load(links, cb, d, u);
+    transport_apply(u, psi, out);
 }
 
 // The group's links (spb sites x 8 directions x 20 floats), staged once per group by the whole CTA;
@@ -436,9 +444,19 @@ __global__ void __launch_bounds__(128) k_net_layer12_tc(NetLayerArgs a) {
                 for (int k = 0; k < 24; ++k) v[k] += wown[k];
             if (a.mix) {
                 __syncwarp();  // the warp's rows of sh are free (previous channel read)
-                row24_store(sh + (size_t)tid * 24, v);
-                __syncwarp();
-                s_mix16_tc(afr, sh, lane, warp, tid, v, false);
+                if (a.sop != SOP_DENSE) {
+                    // structured A^{-1} (or its transpose) by the column pass of the site's 16 lanes
+                    float* site = sh + ls * kSSite<float>;
+                    row24_store(site + s * kSRow<float>, v);
+                    __syncwarp();
+                    s_struct_col<float, kStructNs>(a.sc, a.sop, site, kSRow<float>, s);
+                    __syncwarp();
+                    row24_load(site + s * kSRow<float>, v, false);
+                } else {
+                    row24_store(sh + (size_t)tid * 24, v);
+                    __syncwarp();
+                    s_mix16_tc(afr, sh, lane, warp, tid, v, false);
+                }
             }
             if (!a.own_in_mix && co == 0)
 #pragma unroll
@@ -658,13 +676,23 @@ __global__ void __launch_bounds__(256) k_net_layer_mt(NetLayerArgs a) {
         for (int k = 0; k < 24; ++k) v[k] = a.c_hop * v[k] + (a.own_in_mix ? wown[k] : 0.f);
         if (a.mix) {
             __syncthreads();
-            row24_store(sh + (ls * Ns + s) * 24, v);
-            if (tc) {
+            if (a.sop != SOP_DENSE && Ns == kStructNs) {
+                // structured A^{-1} (or its transpose): the site's 16 threads are lanes of one warp
+                float* site = sh + ls * kSSite<float>;
+                row24_store(site + s * kSRow<float>, v);
                 __syncwarp();
-                s_mix16_tc(afr, sh, lane, warp, ls * Ns + s, v, false);
+                s_struct_col<float, kStructNs>(a.sc, a.sop, site, kSRow<float>, s);
+                __syncwarp();
+                row24_load(site + s * kSRow<float>, v, false);
             } else {
-                __syncthreads();
-                s_mix(mix, sh + ls * Ns * 24, s, Ns, v, false);
+                row24_store(sh + (ls * Ns + s) * 24, v);
+                if (tc) {
+                    __syncwarp();
+                    s_mix16_tc(afr, sh, lane, warp, ls * Ns + s, v, false);
+                } else {
+                    __syncthreads();
+                    s_mix(mix, sh + ls * Ns * 24, s, Ns, v, false);
+                }
             }
         }
         if (!a.own_in_mix)
@@ -977,6 +1005,12 @@ int net_layer(odwf_net_s* n, int parity, int cin, int cout, const float* const* 
     a.nbr = h->nbr[parity];
     a.Vh = h->Vh;
     a.Ns = h->Ns;
+    // the structured form of A^{-1} / A^{-T} (n->mats / n->mats + 2 Ns^2) where it exists
+    a.sop = SOP_DENSE;
+    if (mix && n->sc.has_st && h->Ns == kStructNs) {
+        a.sc = n->sc.st;
+        a.sop = (mix == n->mats) ? SOP_AINV : (SOP_AINV | SOP_T);
+    }
     const int spb = spb_for(h->Ns);
     // the 2 -> 1 layer keeps its transport sums in registers and needs no D-fragment rows (cout 0)
     const size_t smem = layer_smem(h, (cin == 2 && cout == 1) ? 0 : cout);
@@ -1105,6 +1139,9 @@ int net_loss_grad(odwf_net_s* n, double* loss_out, cudaStream_t st) {
     const int C = n->C, NN = h->Ns * h->Ns;
     const double* Ainv = n->mats;
     const double* AinvT = n->mats + 2 * NN;
+    if (n->loss_mode == ODWF_NET_LOSS_ERROR)
+        for (double ne : n->pair_ne)
+            if (!(ne > 0.0)) return set_err(h, ODWF_EINVAL, "error loss: the training pairs were set without e");
     int rc = net_prep(n, st);
     if (rc) return rc;
     // gradient layout in doubles: W0 (32), W1 (C*8*32), W2 (C*8*32) -- the wgrad kernels write
@@ -1318,6 +1355,9 @@ extern "C" int odwf_net_set_pairs(odwf_net_t* n, double m1, double m2, int npair
         if ((rc = launch_pack5(h, (const double*)r[i], rf, h->ws.b_o, ST_FLOAT, 0, st))) return rc;
         if (e && e[i]) {
             if ((rc = launch_pack5(h, (const double*)e[i], ef, h->ws.b_o, ST_FLOAT, 0, st))) return rc;
+        } else if (n->loss_mode == ODWF_NET_LOSS_RESIDUAL) {
+            // the residual loss never reads e_i: no solve (|e_i|^2 = 0 marks the pair as without e)
+            if ((rc = cuda_check(h, cudaMemsetAsync(ef, 0, half32(h), st), "memset"))) return rc;
         } else {
             // D_T x = (r_e, 0) gives x_e = S^{-1} r_e (b_hat = r_e when the odd source vanishes)
             if ((rc = launch_pack5(h, (const double*)r[i], h->ws.b_e, h->ws.b_o, ST_DOUBLE, 0, st))) return rc;

@@ -117,6 +117,8 @@ struct HopArgs {
     long long wait_cycles;  // limit of the bulk-copy wait in SM clock cycles (0: the default, ~1 s)
     int sop;             // SOP_*: structured form of the Mhop / Mown matrix (SOP_DENSE: use the matrix)
     SStruct sc;          // its coefficients (used when sop != SOP_DENSE and Ns == kStructNs)
+    const float* links12;  // two-slice kernels: [Vh][8][12] first two rows of each (unsigned) SU(3) link
+    const int* nbrs;       // two-slice kernels: nbr with ~index where the link carries the sign -1
 };
 
 // ---- host-side handle --------------------------------------------------------------------------
@@ -127,6 +129,8 @@ struct TuneChoice {
     int staged = 0;
     int spbm = 1;
     int dense = 0;  // 1: the dense Ns x Ns fifth-dimension product even where the structured one applies
+    int pair = 0;   // two-slices-per-thread kernel (hop_pair.cu) where it applies: 1 register gathers,
+                    // 2 / 3 bulk-copy gathers through 2 / 3 shared-memory stages
 };
 
 struct SCoef {
@@ -165,6 +169,14 @@ struct odwf_s {
     // links, per output parity: FP64 [Vh][8][18], FP32 [Vh][8][20], FP16 [Vh][8][24 halves]
     double* U64[2] = {nullptr, nullptr};
     float* U32[2] = {nullptr, nullptr};
+    // two-row links of the two-slice kernels, [Vh][8][12] FP32, and the signed neighbour table
+    float* U12[2] = {nullptr, nullptr};
+    int* nbrs[2] = {nullptr, nullptr};
+    unsigned int* u12_dev = nullptr;       // device: max |row 2 - conj(row 0 x row 1)| over the links (float bits)
+    unsigned int* u12_dev_host = nullptr;  // pinned mirror
+    bool links12_ok = false;               // the links are SU(3) to FP32 accuracy: two rows determine them
+    int pair = -1;                         // two-slice kernels (ODWF_PAIR): -1 the tuned choice, 0 never, 1 / 2 / 3 that
+                                           // form wherever it applies
     bool have_gauge = false;
     std::map<std::pair<double, double>, odwf::SCoef> coefs;
     // reductions
@@ -259,9 +271,23 @@ int launch_norm2(odwf_s* h, const void* v, int storage, const float* scale, int 
                  CGState* state = nullptr, double* partials = nullptr);
 void hop_fill(odwf_s* h, int storage, int parity, HopArgs& a, bool reduces);
 int launch_hop_own_cgb(odwf_s* h, int storage, HopArgs a, cudaStream_t st);
+// several systems (blockIdx.y), one launch; structured: every system's arguments carry the structured
+// fifth-dimension products (set_sop with coefficients that have them) and Ns = kStructNs
 int launch_hop_multi(odwf_s* h, int storage, bool mixhop, bool own, bool mixown, int epi, const HopArgs* dev_args,
-                     int n, int max_vh, cudaStream_t st);
+                     int n, int max_vh, cudaStream_t st, bool structured = false);
 int launch_gauge(odwf_s* h, const double* U, cudaStream_t st);
+// grid of a fused kernel for grid mode `mode` (0 one resident wave, 1 one CTA per site group, 2 / 3
+// two / four waves), occupancy occ CTAs per SM, `groups` site groups
+int grid_for_mode(const odwf_s* h, int mode, int occ, int groups, bool reduces);
+// two-slices-per-thread hop kernels (hop_pair.cu): whether a variant has one, and its launch (a filled
+// by hop_fill; spbm the tile multiplier of 16 sites per CTA); key = the profiling key of the launch
+bool pair_variant(int storage, bool mixhop, bool own, bool mixown, int epi);
+bool pair_applies(const odwf_s* h, int storage, const HopArgs& a);
+// form 1: neighbours gathered into registers; 2 / 3: gathered by bulk copies through 2 / 3 shared-memory
+// stages (FP32 storage with 16-byte aligned fields, else form 1)
+int launch_hop_pair(odwf_s* h, int storage, bool mixhop, bool own, bool mixown, int epi, const HopArgs& a,
+                    int mode, int spbm, cudaStream_t st, int form = 1);
+bool pair_tma_applies(int storage, const HopArgs& a);
 int launch_init_state(odwf_s* h, cudaStream_t st);
 void prof_begin(odwf_s* h, int key, cudaStream_t st, cudaEvent_t* a);
 void prof_end(odwf_s* h, int key, cudaStream_t st, cudaEvent_t a);

@@ -255,16 +255,18 @@ static int enqueue_chunk(std::vector<Slot>& S, const HopArgs* dargs, int iters, 
     const int n = (int)S.size();
     odwf_s* h0 = S[0].h;
     const int stg = S[0].f.stg;
+    bool sn = h0->Ns == kStructNs;
+    for (const Slot& s : S) sn = sn && s.c->has_st;
     int rc;
     for (int i = 0; i < iters; ++i) {
         if (n == 1) {
             if ((rc = k1(S[0], false, st)) || (rc = k2a(S[0], st)) || (rc = k1(S[0], true, st)) || (rc = k2b(S[0], st)))
                 return rc;
         } else {
-            if ((rc = launch_hop_multi(h0, stg, true, false, false, EPI_STORE, dargs + 0 * n, n, max_vh, st))) return rc;
-            if ((rc = launch_hop_multi(h0, stg, false, true, true, EPI_CG_A, dargs + 1 * n, n, max_vh, st))) return rc;
-            if ((rc = launch_hop_multi(h0, stg, true, false, false, EPI_STORE, dargs + 2 * n, n, max_vh, st))) return rc;
-            if ((rc = launch_hop_multi(h0, stg, false, true, true, EPI_CG_B, dargs + 3 * n, n, max_vh, st))) return rc;
+            if ((rc = launch_hop_multi(h0, stg, true, false, false, EPI_STORE, dargs + 0 * n, n, max_vh, st, sn))) return rc;
+            if ((rc = launch_hop_multi(h0, stg, false, true, true, EPI_CG_A, dargs + 1 * n, n, max_vh, st, sn))) return rc;
+            if ((rc = launch_hop_multi(h0, stg, true, false, false, EPI_STORE, dargs + 2 * n, n, max_vh, st, sn))) return rc;
+            if ((rc = launch_hop_multi(h0, stg, false, true, true, EPI_CG_B, dargs + 3 * n, n, max_vh, st, sn))) return rc;
         }
     }
     return ODWF_OK;

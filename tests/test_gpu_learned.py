@@ -144,6 +144,23 @@ def test_train_and_solve(env):
     assert st["iters"] <= 1.05 * st2["iters"]
 
 
+def test_residual_loss_pairs_need_no_solves(env):
+    """With the residual loss selected first, set_pairs stores the r_i without solving for e_i; training
+    still lowers the loss, and switching to the error loss on those pairs is refused (ODWF_EINVAL)."""
+    binding, lat, op, U, om = env
+    net = binding.Net(lat, 2)
+    net.set_loss("residual")
+    rs = [torch.from_numpy(inputs.gaussian_spinor5(DIMS, NS, 70 + i)).cuda() for i in range(2)]
+    net.set_pairs(rs, M1, M2)
+    losses = net.train(10, 2e-3)
+    assert losses[-1] < losses[0]
+    net.set_loss("error")
+    with pytest.raises(binding.OdwfError) as ei:
+        net.loss_grad()
+    assert ei.value.code == binding.ODWF_EINVAL
+    net.close()
+
+
 @pytest.mark.parametrize("which,truncate", [("none", False), ("neumann", False), ("trained", False),
                                             ("neumann", True), ("none", True)])
 def test_gcr_solve(env, which, truncate):

@@ -220,6 +220,30 @@ def test_solve_multi_uneven_lattices(lib):
         assert res <= 1.05e-10
 
 
+@pytest.mark.parametrize("prec", ["single", "half"])
+def test_solve_batch_and_multi_structured(lib, prec):
+    """Ns = 16: the batched and multi-lattice launches run the structured fifth-dimension products (one
+    launch per step for all systems); every system meets the FP64 true residual 1e-10 with the oracle."""
+    Ns = 16
+    lat, op, U, om = _setup(lib, (4, 4, 4, 8), Ns, "zolo", 0.3, 11)
+    m12 = [(0.01, 0.01), (0.01, 0.1), (1.0, 0.1)]
+    bs = [inputs.gaussian_spinor5((4, 4, 4, 8), Ns, 700 + i) for i in range(len(m12))]
+    xs, stats = lat.solve_batch([torch.from_numpy(b).cuda() for b in bs], m12,
+                                opts=lib.solve_opts(tol=1e-10, prec=prec))
+    for b, x, (m1, m2), st in zip(bs, xs, m12, stats):
+        res = np.linalg.norm(b - op.ht(x.cpu().numpy(), m1, m2)) / np.linalg.norm(b)
+        assert st["true_residual"] <= 1e-10 and res <= 1.05e-10, (m1, m2, res)
+    lat2, op2, U2, _ = _setup(lib, (4, 4, 2, 6), Ns, "zolo", 0.3, 12)
+    b2 = inputs.gaussian_spinor5((4, 4, 2, 6), Ns, 710)
+    xs, stats = lib.solve_multi([lat, lat2], [torch.from_numpy(bs[0]).cuda(), torch.from_numpy(b2).cuda()],
+                                [(0.01, 0.01), (0.05, 0.1)], opts=lib.solve_opts(tol=1e-10, prec=prec))
+    for o, b, x, (m1, m2) in zip((op, op2), (bs[0], b2), xs, [(0.01, 0.01), (0.05, 0.1)]):
+        res = np.linalg.norm(b - o.ht(x.cpu().numpy(), m1, m2)) / np.linalg.norm(b)
+        assert res <= 1.05e-10, res
+    lat.close()
+    lat2.close()
+
+
 @pytest.mark.parametrize("case", [CASES[0], CASES[2], CASES[3]])
 def test_staged_and_plain_kernels_agree(lib, case, monkeypatch):
     """The bulk-staged FP32/FP16 hop kernels and the per-thread-gather kernels compute the same sums."""

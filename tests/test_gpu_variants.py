@@ -8,6 +8,8 @@
 * The bulk-staged hop kernels (ODWF_STAGED=1) in FP32 (2e-6, as the plain FP32 kernels) and FP16,
   applies and solves; the solve bar is the FP64 true residual 1e-10 for every inner precision.
 * The launch configuration the autotuner picks (odwf_autotune), applies and solves.
+* The two-slices-per-thread kernels with two-row SU(3) links (ODWF_PAIR=1) in FP32 and FP16, applies and
+  a solve, and the one-slice kernels kept for links that are not SU(3).
 * Failure statuses in the allowed forms: a wall-clock budget that runs out (ODWF_ETIMEOUT), a NaN in
   the right-hand side (ODWF_EBREAKDOWN), and the bulk-staged kernels' bounded wait made to run out by a
   test-only cycle limit (ODWF_EFAULT). After each, the device and a fresh handle still work.
@@ -116,6 +118,46 @@ def test_autotuned_variants(lib, prec):
     lat.close()
 
 
+@pytest.mark.parametrize("prec,form", [("single", "1"), ("single", "2"), ("single", "3"), ("half", "1"),
+                                       ("half", "3")])
+def test_two_slice_kernels(lib, prec, form, monkeypatch):
+    """The two-slices-per-thread kernels with two-row links (ODWF_PAIR=form; Ns = 16, structured
+    fifth-dimension products) against the oracle: applies, a solve to the FP64 true residual 1e-10, and
+    the profile shows that they ran (kernel keys 5xxxxx above the one-slice ones; the bulk-copy forms 2
+    and 3 add 1000000 and exist for FP32 storage, FP16 storage keeps the register gathers)."""
+    monkeypatch.setenv("ODWF_PAIR", form)
+    case = CASES[2]
+    lat, op = _setup(lib, *case)
+    lat.profile(True)
+    _apply_checks(lat, op, case, (0.05, 0.5), prec)
+    b = inputs.gaussian_spinor5(case[0], case[1], 260)
+    x, st = lat.solve(torch.from_numpy(b).cuda(), 0.05, 0.1, opts=lib.solve_opts(tol=1e-10, prec=prec))
+    res = np.linalg.norm(b - op.ht(x.cpu().numpy(), 0.05, 0.1)) / np.linalg.norm(b)
+    assert res <= 1.05e-10, res
+    stg = {"single": 1, "half": 2}[prec]
+    bulk = 1000000 if (prec == "single" and form in ("2", "3")) else 0
+    ran = {k for k in lat.profile_read() if (k // 100000) % 10 == stg + 5}
+    # K1 (hop then A^-1), K2A / K2B (A on p plus the hop, CGNE updates) and the apply's hop + A own
+    assert {bulk + stg * 100000 + 500000 + k for k in (11000, 10112, 10113, 10110)} <= ran, ran
+    lat.close()
+
+
+def test_two_slice_kernels_need_su3_links(lib, monkeypatch):
+    """Links that are not SU(3) (here 1.01 U) are not represented by two rows: the library keeps the
+    one-slice kernels, and the results still agree with the oracle."""
+    monkeypatch.setenv("ODWF_PAIR", "1")
+    dims, Ns = CASES[2][0], CASES[2][1]
+    om = inputs.omega_zolotarev(Ns, 0.05, 6.2)
+    U = 1.01 * inputs.random_su3_links(dims, 0.3, 3)
+    lat = lib.ODWF(dims, Ns, 1.3, om)
+    lat.set_gauge(torch.from_numpy(U).cuda())
+    op = OracleODWF(U, 1.3, om)
+    lat.profile(True)
+    _apply_checks(lat, op, CASES[2], (0.05, 0.5), "single")
+    assert not any((k // 100000) % 10 >= 5 for k in lat.profile_read() if k < 1000000)
+    lat.close()
+
+
 def test_timeout_status_and_recovery(lib):
     lat, op = _setup(lib, *CASES[2])
     b = torch.from_numpy(inputs.gaussian_spinor5(CASES[2][0], CASES[2][1], 31)).cuda()
@@ -157,6 +199,26 @@ def test_staged_wait_timeout_status(lib, monkeypatch):
         lat.apply(x, 0.05, 0.5, op="dt", prec="single")
     assert e.value.code == lib.ODWF_EFAULT
     # the fault word was cleared: with the normal limit the same handle type works again
+    lat.close()
+    monkeypatch.delenv("ODWF_TEST_WAIT_CYCLES")
+    lat2, op2 = _setup(lib, *case)
+    assert _rel(lat2.apply(x, 0.05, 0.5, op="dt", prec="single").cpu().numpy(), op2.dt(psi, 0.05, 0.5)) < TOL_SINGLE
+    lat2.close()
+
+
+def test_two_slice_bulk_wait_timeout_status(lib, monkeypatch):
+    """The same one-cycle wait limit on the bulk-copy two-slice kernels (ODWF_PAIR=3): the waits run out,
+    the kernel stops issuing, waits out the copies in flight with the normal limit and returns; the call
+    reports ODWF_EFAULT and a fresh handle computes D_T correctly."""
+    case = CASES[2]
+    monkeypatch.setenv("ODWF_PAIR", "3")
+    monkeypatch.setenv("ODWF_TEST_WAIT_CYCLES", "1")
+    lat, op = _setup(lib, *case)
+    psi = inputs.gaussian_spinor5(case[0], case[1], 34)
+    x = torch.from_numpy(psi).cuda()
+    with pytest.raises(lib.OdwfError) as e:
+        lat.apply(x, 0.05, 0.5, op="dt", prec="single")
+    assert e.value.code == lib.ODWF_EFAULT
     lat.close()
     monkeypatch.delenv("ODWF_TEST_WAIT_CYCLES")
     lat2, op2 = _setup(lib, *case)
