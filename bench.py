@@ -726,11 +726,28 @@ def main():
     if not args.no_fp64:
         barrier()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        lat.profile(True)
         f0.record(stream)
         _, st64 = lat.solve(b, MASS, MASS, opts=solve_opts(tol=TOL, prec="double"))
         f1.record(stream)
         barrier()
+        prof64 = lat.profile_read()
+        lat.profile(False)
         fp64 = {"seconds": f0.elapsed_time(f1) / 1e3, "iters": st64["iters"], "true_residual": st64["true_residual"]}
+        # the FP64 hop kernels against the measured FP64 FMA roof (flop conventions of HOP_FLOPS / FIFTH_FLOPS)
+        peak64 = lat.fp64_fma_peak()
+        Vh = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] // 2
+        roof = []
+        for key, (n, ms) in sorted(prof64.items(), key=lambda kv: -kv[1][1]):
+            if key >= 1000000 or (key // 100000) % 10 != 0 or n == 0:
+                continue
+            hop, mixhop, mixown = (key // 10000) % 10, (key // 1000) % 10, (key // 10) % 10
+            fl = Vh * NS * (HOP_FLOPS * hop + FIFTH_FLOPS * (mixhop + mixown))
+            tf = fl / (ms / n * 1e-3) / 1e12
+            roof.append({"kernel": kernel_name(key), "launches": n, "avg_us": ms / n * 1e3, "tflops": tf,
+                         "frac_of_fp64_peak": tf / peak64})
+        fp64["fp64_fma_peak_tflops"] = peak64
+        fp64["fp64_kernels"] = roof
 
     def timed(fn):
         barrier()

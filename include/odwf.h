@@ -297,9 +297,11 @@ int eofa_solve_gcr(odwf_t* h, odwf_net_t* net, double m1, double m2, const void*
                    const odwf_solve_opts* opts, odwf_solve_stats* stats, void* stream);
 
 /* Autotuner: times the launch choices (fifth-dimension form at Ns = 16: the structured recurrence or the
- * dense Ns x Ns product; tile: the default number of sites per CTA or twice it, as long
- * as the CTA stays within 256 threads; grid size: one resident wave, one CTA per site group, two or
- * four waves; per-thread neighbour gathers or bulk-staged gathers) of the four fused kernels of the
+ * dense Ns x Ns product; at Ns = 16 with SU(3) links the two-slices-per-thread kernels with two-row links,
+ * their neighbours gathered into registers or by bulk copies through 2 or 3 shared-memory stages; tile:
+ * the default number of sites per CTA or twice it, as long as the CTA stays within 256 threads; grid
+ * size: one resident wave, one CTA per site group, two or four waves; per-thread neighbour gathers or
+ * bulk-staged gathers) of the four fused kernels of the
  * CGNE iteration in precision prec on this handle's lattice and keeps the fastest for later calls.
  * report (may be NULL) receives the timings as text. Overwrites the handle's inner work fields and
  * solver state; call it between solves. The paper has no counterpart (a tuning aid). */
@@ -308,8 +310,14 @@ int odwf_autotune(odwf_t* h, int prec, char* report, int report_len, void* strea
 /* Persisted autotuner choices: if the text file `path` holds an entry for this device name, lattice,
  * Ns and precision, its choices are applied (*hit = 1, no timing); otherwise odwf_autotune runs and
  * its choices are appended to the file as one line (*hit = 0). Returns ODWF_EINVAL if the file cannot
- * be appended to. Entries are plain text: device|LxxLyxLzxLt|Ns|prec|key:grid-mode:staged:tile:dense,... */
+ * be appended to. Entries are plain text: device|LxxLyxLzxLt|Ns|prec|key:grid-mode:staged:tile:dense:two-slice,...
+ * (two-slice: 0 none, 1 register gathers, 2 / 3 bulk-copy stages; older 5-field entries read it as 0) */
 int odwf_autotune_cache(odwf_t* h, int prec, const char* path, int* hit, void* stream);
+
+/* Measured FP64 FMA throughput of the current device in TFLOP/s (independent FMA chains on every SM,
+ * CUDA-event timed): the roof of the FP64 hop kernels, which the double-precision pipe bounds rather
+ * than HBM. A measurement aid with no counterpart in the paper; allocates and frees a small buffer. */
+int odwf_fp64_fma_peak(odwf_t* h, double* tflops, void* stream);
 
 /* Kernel timing for measurement: while enabled, every launch of the library's kernels on this
  * handle (hopping, network, GCR, layout and vector kernels) is bracketed by CUDA events on its

@@ -34,7 +34,7 @@ EXPORTS = ["odwf_create", "odwf_destroy", "odwf_last_error", "odwf_set_gauge", "
            "odwf_net_num_params", "odwf_net_weights", "odwf_net_apply", "odwf_net_set_pairs", "odwf_net_loss_grad",
            "odwf_net_train", "eofa_solve_learned", "odwf_autotune", "eofa_solve_gcr", "eofa_term_spectrum",
            "hmc_gauge_action", "hmc_gauge_force", "hmc_momentum_update", "hmc_link_update", "hmc_kinetic",
-           "hmc_md", "odwf_autotune_cache", "odwf_net_set_loss", "odwf_set_preconditioner"]
+           "hmc_md", "odwf_autotune_cache", "odwf_net_set_loss", "odwf_set_preconditioner", "odwf_fp64_fma_peak"]
 
 
 class OdwfError(RuntimeError):
@@ -123,6 +123,7 @@ def load_library(path: str = LIB_PATH):
     lib.eofa_k.argtypes = [d, d]
     lib.eofa_k.restype = d
     lib.odwf_omega_vector.argtypes = [vp, i, dp]
+    lib.odwf_fp64_fma_peak.argtypes = [vp, dp, vp]
     lib.odwf_profile_enable.argtypes = [vp, i]
     lib.odwf_profile_read.argtypes = [vp, ip, ip, dp, ip]
     lib.eofa_mp_terms.argtypes = [i, d, dp, i, d, i, ctypes.POINTER(Term), i, ip]
@@ -383,6 +384,12 @@ class ODWF:
         buf = ctypes.create_string_buffer(1 << 16)
         self._check(self.lib.odwf_autotune(self.h, _PREC[prec], buf, 1 << 16, _stream_ptr(stream)))
         return buf.value.decode()
+
+    def fp64_fma_peak(self, stream=None):
+        """Measured FP64 FMA throughput of the device (TFLOP/s)."""
+        t = ctypes.c_double()
+        self._check(self.lib.odwf_fp64_fma_peak(self.h, ctypes.byref(t), _stream_ptr(stream)))
+        return t.value
 
     def set_preconditioner(self, net):
         """Attach a Net (or None) for the solves of action, force and the MD trajectory."""

@@ -21,7 +21,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libodwf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "eofa.cu", "solver.cpp", "api.cpp", "noalloc.cu", "learned.cu", "hmc.cu", "hop_pair.cu"]
+SOURCES = ["kernels.cu", "eofa.cu", "solver.cpp", "api.cpp", "noalloc.cu", "learned.cu", "hmc.cu", "hop_pair.cu", "peak.cu"]
 
 
 def nvcc() -> str:

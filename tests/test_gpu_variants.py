@@ -305,3 +305,12 @@ def test_autotune_cache_persists_and_tiles(lib, tmp_path):
         x, st = lat3.solve(torch.from_numpy(b).cuda(), 0.05, 0.1, opts=lib.solve_opts(tol=1e-10, prec="single"))
         assert np.linalg.norm(b - op3.ht(x.cpu().numpy(), 0.05, 0.1)) / np.linalg.norm(b) <= 1.05e-10
         lat3.close()
+
+
+def test_fp64_fma_peak_measured(lib):
+    """The FP64 roof the FP64 hop kernels are reported against is measured on the device: positive and
+    below the FP32 rate (GB300 runs FP64 at a small fraction of it)."""
+    lat, op = _setup(lib, *CASES[0])
+    t = lat.fp64_fma_peak()
+    assert 0.05 < t < 20.0, t
+    lat.close()
