@@ -28,6 +28,19 @@ def test_hop_kernel_bytes():
     assert bench.alg_bytes(k1h, VH, NS) == VH * NS * 2 * (48 + 4) + VH * 8 * 18 * 4
 
 
+def test_two_slice_kernel_names_and_bytes():
+    # the two-slice kernels (storage digit + 5) read links as two rows: 8 x 12 reals per 4D half-site
+    k1p = 600000 + 10000 + 1000
+    assert bench.kernel_name(k1p) == "k_hop<two-slice,fp32,hop+A^-1,store>"
+    assert bench.alg_bytes(k1p, VH, NS) == VH * NS * 48 * 4 + VH * 8 * 12 * 4
+    # their bulk-copy form adds 1000000 to the key, like the bulk-staged kernels, with its own name
+    assert bench.kernel_name(1000000 + k1p) == "k_hop<two-slice bulk,fp32,hop+A^-1,store>"
+    assert bench.alg_bytes(1000000 + k1p, VH, NS) == bench.alg_bytes(k1p, VH, NS)
+    assert bench.kernel_name(1000000 + 111000) == "k_hop<staged,fp32,hop+A^-1,store>"
+    # FP16 two-slice: storage digit 7
+    assert bench.kernel_name(700000 + 10000 + 100 + 10 + 3) == "k_hop<two-slice,fp16,hop+A*own,cg_b>"
+
+
 def test_network_layer_bytes():
     # FP32 fields of 96 bytes per 5D half-site; BF16 intermediates are 48-byte rows per channel
     assert bench.alg_bytes(2000120, VH, NS) == VH * NS * (96 + 2 * 96) + VH * 8 * 18 * 4
