@@ -381,7 +381,7 @@ def md_step(lat, binding, inputs, dims, U, opts, opts_ref, beta, dtau, rank):
     # (Neumann-initialised: no training cost) attached to the handle
     net = binding.Net(lat, channels=2)
     lat.set_preconditioner(net)
-    lopts = binding.solve_opts(tol=opts.tol, prec="single", delta=1e-3)
+    lopts = binding.solve_opts(tol=opts.tol, prec="single", delta=1e-4)
     for t, phi, r in zip(terms, phis, rec):
         ta = time.perf_counter()
         S_n, st_an = lat.action(t, phi, opts=lopts)
@@ -438,7 +438,7 @@ def hmc_trajectory(lat, binding, inputs, dims, U, opts, beta, rank, steps=PAPER_
     net = binding.Net(lat, channels=2)
     lat.set_preconditioner(net)
     st = lat.md(Ux, P, beta, terms, phis, paper_levels(len(terms)), list(steps), tau=1.0,
-                opts=binding.solve_opts(tol=opts.tol, prec="single", delta=1e-3))
+                opts=binding.solve_opts(tol=opts.tol, prec="single", delta=1e-4))
     torch.cuda.synchronize()
     lat.set_preconditioner(None)
     net.close()
@@ -517,7 +517,7 @@ def config4(args):
         train_log.append({"config": c, "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
                           "seconds": t_tr})
     t_train = time.perf_counter() - t_start
-    opts_l = solve_opts(tol=TOL, prec="single", delta=1e-3)
+    opts_l = solve_opts(tol=TOL, prec="single", delta=1e-4)
     opts_p = solve_opts(tol=TOL, prec="single", delta=0.01)
     evals = []
     for h in range(args.c4_heldout):
@@ -585,6 +585,9 @@ def main():
     ap.add_argument("--dims", default=None, help="override lattice, e.g. 16,16,16,16 (profiling only)")
     ap.add_argument("--beta", type=float, default=6.2, help="Wilson plaquette coupling of the MD sections")
     ap.add_argument("--no-hmc", action="store_true", help="skip the HMC trajectory section")
+    ap.add_argument("--net-delta", type=float, default=1e-4,
+                    help="the learned solve's reliable-update trigger: an FP64 residual whenever the FP32 one has "
+                         "dropped by this factor")
     ap.add_argument("--config4", action="store_true",
                     help="instead of the default workload: the network trained across seeded configurations and "
                          "evaluated on held-out ones (32^3 x 64, m = 0.005)")
@@ -660,7 +663,7 @@ def main():
                          "train_steps": args.train_steps, "lr": args.lr,
                          "train_seconds": t2 - t1, "loss_first": float(losses[0]), "loss_last": float(losses[-1])}
         del rs
-        lopts = solve_opts(tol=TOL, prec="single", delta=1e-3)
+        lopts = solve_opts(tol=TOL, prec="single", delta=args.net_delta)
 
         if args.method == "learned":
             def do_solve(bb, xx=None):
@@ -836,10 +839,10 @@ def main():
         # preconditioned solve with the untrained (Neumann-series) network, and, when the timed method
         # is plain CGNE, with a trained one
         neu = Net(lat, channels=2)
-        (xn, stn), t_n = timed(lambda: neu.solve(b, MASS, MASS, opts=solve_opts(tol=TOL, prec="single", delta=1e-3)))
+        (xn, stn), t_n = timed(lambda: neu.solve(b, MASS, MASS, opts=solve_opts(tol=TOL, prec="single", delta=args.net_delta)))
         extra["neumann_network_solve"] = {"seconds": t_n, "iters": stn["iters"], "true_residual": stn["true_residual"]}
         if args.method == "gcr":
-            (_, stp), t_p = timed(lambda: net.solve(b, MASS, MASS, opts=solve_opts(tol=TOL, prec="single", delta=1e-3)))
+            (_, stp), t_p = timed(lambda: net.solve(b, MASS, MASS, opts=solve_opts(tol=TOL, prec="single", delta=args.net_delta)))
             extra["learned_pcgne"] = {"seconds": t_p, "iters": stp["iters"], "true_residual": stp["true_residual"]}
         neu.close()
     if args.gcr_sweep:
@@ -931,7 +934,7 @@ def main():
         "clocks": clk.summary(),
         "autotune": tune_report,
         "method": {"learned": "CGNE on S M with the trained gauge-equivariant network M (BF16 tensor-core "
-                              "channel mixing), FP32 inner cycles restarted from the FP64 residual",
+                              "channel mixing), FP32 inner cycles with FP64 reliable updates",
                    "gcr": f"flexible GCR ({args.nvec} directions, {'sliding window' if args.truncate else 'restarted'}) "
                           "on S right-preconditioned by the trained network, FP32 inner cycles restarted from the "
                           "FP64 residual",

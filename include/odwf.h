@@ -271,14 +271,15 @@ int odwf_net_loss_grad(odwf_net_t* net, double* loss, double* grad, void* stream
 /* steps Adam updates with learning rate lr on the stored pairs; losses[steps + 1] may be NULL. */
 int odwf_net_train(odwf_net_t* net, int steps, double lr, double* losses, void* stream);
 /* Attach net (created on h) so that the single-system solves of eofa_action, eofa_force and hmc_md use
- * the network-preconditioned CGNE of eofa_solve_learned (FP32 inner cycles restarted from the FP64
- * residual whenever it has dropped by opts->delta; opts->prec is not used) instead of plain CGNE; the
+ * the network-preconditioned CGNE of eofa_solve_learned (FP32 inner cycles with FP64 reliable updates
+ * whenever the residual has dropped by opts->delta; opts->prec is not used) instead of plain CGNE; the
  * network applies the fifth-dimension inverse of each solve's own masses, its weights are shared. NULL
  * detaches. The heat-bath keeps the batched plain solver for its poles. Not in the paper. */
 int odwf_set_preconditioner(odwf_t* h, odwf_net_t* net);
 /* H_T(m1, m2) x = b like eofa_solve, with CGNE on S M (right preconditioning by the network, the
- * iterate accumulating x = M y directly), FP32 inner cycles restarted from the FP64 residual
- * whenever it has dropped by opts->delta. */
+ * iterate accumulating x = M y directly), FP32 inner cycles whose residual is replaced by the FP64 one
+ * whenever it has dropped by opts->delta (reliable updates: the search direction and the last beta carry
+ * over into the next cycle). */
 int eofa_solve_learned(odwf_t* h, odwf_net_t* net, double m1, double m2, const void* b, void* x,
                        const odwf_solve_opts* opts, odwf_solve_stats* stats, void* stream);
 /* H_T(m1, m2) x = b like eofa_solve, with flexible GCR on the even-odd Schur system S (Sec. 2, the

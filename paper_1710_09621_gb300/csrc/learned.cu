@@ -312,8 +312,10 @@ __host__ __device__ constexpr size_t layer12_tc_smem() {
     return (size_t)3 * kTcABytes + kTcBBytes + sizeof(uint32_t) * kAfrag16Words + 64;
 }
 
-template <bool OUTB>
-__global__ void __launch_bounds__(128) k_net_layer12_tc(NetLayerArgs a) {
+// MINB > 1 asks the compiler for that many resident CTAs of 128 threads per SM (a register cap of
+// 65536 / (128 MINB)); MINB = 1 leaves the registers to the compiler.
+template <bool OUTB, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_net_layer12_tc(NetLayerArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_tc[];
     constexpr int Ns = 16;
     const int s = threadIdx.x, ls = threadIdx.y, spb = blockDim.y;
@@ -501,8 +503,9 @@ __global__ void __launch_bounds__(128) k_net_layer12_tc(NetLayerArgs a) {
 // as one complex number. Each lane therefore holds all three colours of one spin for four threads
 // of its warp, applies U_d to them and keeps the sums in registers across the eight directions; one
 // shared-memory transpose per site group (not one per direction) hands every thread its own spinor.
-template <bool INB>
-__global__ void __launch_bounds__(256) k_net_layer_mt(NetLayerArgs a) {
+// CTAs of 128 threads, MINB resident per SM asked of the compiler (4: at most 128 registers)
+template <bool INB, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_net_layer_mt(NetLayerArgs a) {
     extern __shared__ __align__(16) unsigned char smem_net[];
     const int Ns = a.Ns;
     const int s = threadIdx.x, ls = threadIdx.y, spb = blockDim.y;
@@ -913,6 +916,10 @@ struct odwf_net_s {
     bool prepped = false;
     double cm1 = -1, cm2 = -1;
     bool use_tc = true;      // the tcgen05 1 -> 2 layer at Ns = 16 (ODWF_TCGEN05=0: the mma.sync layer)
+    // register caps of the two layers (ODWF_NET_OCC=<tc>:<mt>): resident CTAs of 128 threads asked of the
+    // compiler. The tcgen05 layer at 4 (128 registers, 16 bytes spilled) runs 155 us against 170 us at the
+    // 156 registers it takes uncapped (3 CTAs per SM); the 2 -> 1 layer at 5 (96 registers) gains 1 %.
+    int minb_tc = 4, minb_mt = 4;
     double* mats = nullptr;  // transposed A^{-1} (2 Ns^2) then A^{-T} (2 Ns^2), FP64
     SCoef sc{};              // structured form of the same (for the s-mixing kernel; sc.dev unused)
     // FP32 half fields: u (even), v[C] (odd), t (even), gy (even), gh[C] (odd), delta (even)
@@ -1017,7 +1024,7 @@ int net_layer(odwf_net_s* n, int parity, int cin, int cout, const float* const* 
     const dim3 blk(h->Ns, spb);
     auto launch = [&](void (*fn)(NetLayerArgs), int kind) -> int {
         // every layer kernel has the same type: one attribute flag per kernel, not per type
-        static bool set[6] = {false, false, false, false, false, false};
+        static bool set[7] = {false, false, false, false, false, false, false};
         if (!set[kind]) {
             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
             set[kind] = true;
@@ -1035,15 +1042,19 @@ int net_layer(odwf_net_s* n, int parity, int cin, int cout, const float* const* 
         // the tcgen05 layer: its own shared-memory layout and a bounded wait (read by check_fault)
         a.fault = h->fault;
         h->staged_used = true;
-        auto fn = bf16 ? k_net_layer12_tc<true> : k_net_layer12_tc<false>;
-        static bool set_tc[2] = {false, false};
+        const bool cap = n->minb_tc > 1;
+        auto fn = bf16 ? (cap ? k_net_layer12_tc<true, 4> : k_net_layer12_tc<true, 1>)
+                       : (cap ? k_net_layer12_tc<false, 4> : k_net_layer12_tc<false, 1>);
+        const int vi = (bf16 ? 1 : 0) + (cap ? 2 : 0);
+        static bool set_tc[4] = {false, false, false, false};
         const size_t smem_tc = layer12_tc_smem();
-        if (!set_tc[bf16 ? 1 : 0]) {
+        if (!set_tc[vi]) {
             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tc);
-            set_tc[bf16 ? 1 : 0] = true;
+            set_tc[vi] = true;
         }
         // resident CTAs per SM from the kernel's registers, its shared memory and its tensor-memory columns
-        static int occ_tc = 0;
+        static int occ_tcv[4] = {0, 0, 0, 0};
+        int& occ_tc = occ_tcv[vi];
         if (occ_tc == 0) {
             cudaFuncAttributes fa{};
             int dev = 0, smem_sm = 0;
@@ -1063,7 +1074,11 @@ int net_layer(odwf_net_s* n, int parity, int cin, int cout, const float* const* 
         return cuda_check(h, cudaGetLastError(), "k_net_layer12_tc");
     }
     if (cin == 1 && cout == 2) return bf16 ? launch(k_net_layer<1, 2, true>, 0) : launch(k_net_layer<1, 2, false>, 1);
-    if (cin == 2 && cout == 1) return bf16 ? launch(k_net_layer_mt<true>, 2) : launch(k_net_layer_mt<false>, 3);
+    if (cin == 2 && cout == 1) {
+        if (n->minb_mt > 4)
+            return bf16 ? launch(k_net_layer_mt<true, 5>, 5) : launch(k_net_layer_mt<false, 5>, 6);
+        return bf16 ? launch(k_net_layer_mt<true, 4>, 2) : launch(k_net_layer_mt<false, 4>, 3);
+    }
     if (cin == 1 && cout == 1) return launch(k_net_layer<1, 1, false>, 4);
     return net_err(n, ODWF_EINVAL, "unsupported layer shape");
 }
@@ -1231,6 +1246,13 @@ extern "C" int odwf_net_create(odwf_t* h, int channels, odwf_net_t** out) {
     n->h = h;
     n->C = channels;
     if (const char* e = std::getenv("ODWF_TCGEN05")) n->use_tc = (e[0] == '1');
+    if (const char* e = std::getenv("ODWF_NET_OCC")) {
+        int a = 1, b = 0;
+        if (std::sscanf(e, "%d:%d", &a, &b) == 2) {
+            n->minb_tc = a > 1 ? 4 : 1;
+            n->minb_mt = b > 4 ? 5 : 4;
+        }
+    }
     n->P = 16 + 2 * channels * 8 * 16;
     const int C = channels;
     int rc = ODWF_OK;
@@ -1594,20 +1616,28 @@ int odwf::learned_solve(odwf_s* h, odwf_net_s* n, double m1, double m2, const vo
     const double tol2 = o.tol * o.tol * bnorm2;
     int iters = 0, cycles = 0;
     const double delta = (o.delta > 0 && o.delta < 1) ? o.delta : 1e-3;
+    // reliable updates: after the first cycle the search direction and the last beta carry over, so the
+    // FP64 residual replaces the FP32 one without discarding the Krylov space (ODWF_NET_RESTART=1 restarts
+    // each cycle from p = 0 instead)
+    const char* restart_env = std::getenv("ODWF_NET_RESTART");
+    const bool restart = restart_env && restart_env[0] == '1';
+    double beta_keep = 0.0;
     auto S32 = [&](const float* in, float* out, bool dag) -> int { return schur32(h, c, in, t, out, dag, st); };
     while (rr64 > tol2 && iters < o.maxiter) {
         // cycle: solve S M y = r64 to relative delta, x_inner = M y accumulated directly
+        const bool keep = cycles > 0 && !restart;
         if ((rc = launch_convert(h, w.r64, ST_DOUBLE, nullptr, rho, ST_FLOAT, nullptr, st))) return rc;
         if ((rc = cuda_check(h, cudaMemsetAsync(xi, 0, b32, st), "memset"))) return rc;
-        if ((rc = cuda_check(h, cudaMemsetAsync(p, 0, b32, st), "memset"))) return rc;
+        if (!keep && (rc = cuda_check(h, cudaMemsetAsync(p, 0, b32, st), "memset"))) return rc;
         CGState& hs = *h->state_host;
         std::memset(&hs, 0, sizeof(CGState));
         hs.rr = rr64;
         hs.rr_max = rr64;
         hs.tol2 = std::max(0.25 * tol2, delta * delta * rr64);
         hs.maxiter = o.maxiter - iters;
+        hs.beta = keep ? beta_keep : 0.0;
         if ((rc = write_state(h, st))) return rc;
-        // p = M^dag S^dag rho (beta = 0)
+        // p = M^dag S^dag rho + beta p (beta = 0 in the first cycle)
         if ((rc = S32(rho, wv, true))) return rc;
         if ((rc = net_apply_even(n, wv, mv, 1, st))) return rc;
         {
@@ -1655,6 +1685,7 @@ int odwf::learned_solve(odwf_s* h, odwf_net_s* n, double m1, double m2, const vo
             flag = h->state_host->flag;
         }
         iters += h->state_host->iter;
+        beta_keep = h->state_host->beta;
         ++cycles;
         if (flag == FLAG_BREAKDOWN) return set_err(h, ODWF_EBREAKDOWN, "preconditioned CGNE breakdown");
         if ((rc = launch_axpy_to64(h, 1.0, xi, ST_FLOAT, nullptr, (double*)w.x_e, st))) return rc;
