@@ -381,7 +381,7 @@ def md_step(lat, binding, inputs, dims, U, opts, opts_ref, beta, dtau, rank):
     # (Neumann-initialised: no training cost) attached to the handle
     net = binding.Net(lat, channels=2)
     lat.set_preconditioner(net)
-    lopts = binding.solve_opts(tol=opts.tol, prec="single", delta=1e-4)
+    lopts = binding.solve_opts(tol=opts.tol, prec="single", delta=1e-5)
     for t, phi, r in zip(terms, phis, rec):
         ta = time.perf_counter()
         S_n, st_an = lat.action(t, phi, opts=lopts)
@@ -438,7 +438,7 @@ def hmc_trajectory(lat, binding, inputs, dims, U, opts, beta, rank, steps=PAPER_
     net = binding.Net(lat, channels=2)
     lat.set_preconditioner(net)
     st = lat.md(Ux, P, beta, terms, phis, paper_levels(len(terms)), list(steps), tau=1.0,
-                opts=binding.solve_opts(tol=opts.tol, prec="single", delta=1e-4))
+                opts=binding.solve_opts(tol=opts.tol, prec="single", delta=1e-5))
     torch.cuda.synchronize()
     lat.set_preconditioner(None)
     net.close()
@@ -517,7 +517,7 @@ def config4(args):
         train_log.append({"config": c, "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
                           "seconds": t_tr})
     t_train = time.perf_counter() - t_start
-    opts_l = solve_opts(tol=TOL, prec="single", delta=1e-4)
+    opts_l = solve_opts(tol=TOL, prec="single", delta=1e-5)
     opts_p = solve_opts(tol=TOL, prec="single", delta=0.01)
     evals = []
     for h in range(args.c4_heldout):
@@ -585,7 +585,7 @@ def main():
     ap.add_argument("--dims", default=None, help="override lattice, e.g. 16,16,16,16 (profiling only)")
     ap.add_argument("--beta", type=float, default=6.2, help="Wilson plaquette coupling of the MD sections")
     ap.add_argument("--no-hmc", action="store_true", help="skip the HMC trajectory section")
-    ap.add_argument("--net-delta", type=float, default=1e-4,
+    ap.add_argument("--net-delta", type=float, default=1e-5,
                     help="the learned solve's reliable-update trigger: an FP64 residual whenever the FP32 one has "
                          "dropped by this factor")
     ap.add_argument("--config4", action="store_true",
