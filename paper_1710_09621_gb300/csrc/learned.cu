@@ -503,10 +503,8 @@ __global__ void __launch_bounds__(128, MINB) k_net_layer12_tc(NetLayerArgs a) {
 // as one complex number. Each lane therefore holds all three colours of one spin for four threads
 // of its warp, applies U_d to them and keeps the sums in registers across the eight directions; one
 // shared-memory transpose per site group (not one per direction) hands every thread its own spinor.
-// CTAs of 128 threads, MINB resident per SM asked of the compiler (4: at most 128 registers). PF (BF16
-// inputs only): the rows of direction d + 1 are loaded into registers before direction d is multiplied
-// and transported, so their latency overlaps that work.
-template <bool INB, int MINB, bool PF = false>
+// CTAs of 128 threads, MINB resident per SM asked of the compiler (4: at most 128 registers)
+template <bool INB, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_net_layer_mt(NetLayerArgs a) {
     extern __shared__ __align__(16) unsigned char smem_net[];
     const int Ns = a.Ns;
@@ -561,34 +559,14 @@ __global__ void __launch_bounds__(128, MINB) k_net_layer_mt(NetLayerArgs a) {
         for (int h = 0; h < 2; ++h)
 #pragma unroll
             for (int e = 0; e < 2; ++e) lsite[h][e] = (warp * 32 + 16 * h + gid + 8 * e) / Ns;
-        // the BF16 rows of both channels and 3 colours of direction dd at this thread's (site, s)
-        auto load_rows = [&](int dd, uint4 (&q)[2][3]) {
-            const int nn = valid ? __ldg(a.nbr + (size_t)cb * 8 + dd) : 0;
-#pragma unroll
-            for (int ci = 0; ci < 2; ++ci) {
-                const uint4* ip = reinterpret_cast<const uint4*>(a.in[ci]) + (size_t)nn * 3 * Ns + s;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) q[ci][c] = valid ? __ldg(ip + (size_t)c * Ns) : make_uint4(0u, 0u, 0u, 0u);
-            }
-        };
-        uint4 qcur[2][3];
-        if constexpr (PF && INB) load_rows(0, qcur);
 #pragma unroll 1
         for (int d = 0; d < 8; ++d) {
             const int n = valid ? __ldg(a.nbr + (size_t)cb * 8 + d) : 0;
-            uint4 qnext[2][3];
-            if constexpr (PF && INB) {
-                if (d < 7) load_rows(d + 1, qnext);
-            }
             // A rows of this thread, colour-major: row 96 warp + 32 c + lane holds
             // [v_0 re s0..3 | v_0 im | v_1 re | v_1 im] of colour c as BF16
 #pragma unroll
             for (int ci = 0; ci < 2; ++ci) {
-                if constexpr (PF && INB) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        *reinterpret_cast<uint4*>(X + (size_t)(warp * 96 + c * 32 + lane) * kXStride + ci * 8) = qcur[ci][c];
-                } else if constexpr (INB) {
+                if constexpr (INB) {
                     // BF16 rows of the first layer: copied to the A-operand rows as they are
                     const uint4* ip = reinterpret_cast<const uint4*>(a.in[ci]) + (size_t)n * 3 * Ns + s;
 #pragma unroll
@@ -654,14 +632,6 @@ __global__ void __launch_bounds__(128, MINB) k_net_layer_mt(NetLayerArgs a) {
                 }
             }
             __syncwarp();  // X rows are rewritten by the next direction
-            if constexpr (PF && INB) {
-                if (d < 7) {
-#pragma unroll
-                    for (int ci = 0; ci < 2; ++ci)
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) qcur[ci][c] = qnext[ci][c];
-                }
-            }
         }
         // transpose: every lane writes its sums into the served threads' rows of 24 floats, then each
         // thread reads its own spinor. The rows (sh) alias other warps' X rows: CTA barrier first.
@@ -950,9 +920,6 @@ struct odwf_net_s {
     // compiler. The tcgen05 layer at 4 (128 registers, 16 bytes spilled) runs 155 us against 170 us at the
     // 156 registers it takes uncapped (3 CTAs per SM); the 2 -> 1 layer at 5 (96 registers) gains 1 %.
     int minb_tc = 4, minb_mt = 4;
-    // 2 -> 1 inference layer with the next direction's rows prefetched (ODWF_NET_PF): 0 off, 1 at 4 CTAs
-    // per SM, 2 at 3 CTAs per SM
-    int mt_form = 0;
     double* mats = nullptr;  // transposed A^{-1} (2 Ns^2) then A^{-T} (2 Ns^2), FP64
     SCoef sc{};              // structured form of the same (for the s-mixing kernel; sc.dev unused)
     // FP32 half fields: u (even), v[C] (odd), t (even), gy (even), gh[C] (odd), delta (even)
@@ -1057,7 +1024,7 @@ int net_layer(odwf_net_s* n, int parity, int cin, int cout, const float* const* 
     const dim3 blk(h->Ns, spb);
     auto launch = [&](void (*fn)(NetLayerArgs), int kind) -> int {
         // every layer kernel has the same type: one attribute flag per kernel, not per type
-        static bool set[9] = {false, false, false, false, false, false, false, false, false};
+        static bool set[7] = {false, false, false, false, false, false, false};
         if (!set[kind]) {
             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
             set[kind] = true;
@@ -1108,8 +1075,6 @@ int net_layer(odwf_net_s* n, int parity, int cin, int cout, const float* const* 
     }
     if (cin == 1 && cout == 2) return bf16 ? launch(k_net_layer<1, 2, true>, 0) : launch(k_net_layer<1, 2, false>, 1);
     if (cin == 2 && cout == 1) {
-        if (bf16 && n->mt_form == 1) return launch(k_net_layer_mt<true, 4, true>, 7);
-        if (bf16 && n->mt_form == 2) return launch(k_net_layer_mt<true, 3, true>, 8);
         if (n->minb_mt > 4)
             return bf16 ? launch(k_net_layer_mt<true, 5>, 5) : launch(k_net_layer_mt<false, 5>, 6);
         return bf16 ? launch(k_net_layer_mt<true, 4>, 2) : launch(k_net_layer_mt<false, 4>, 3);
@@ -1281,7 +1246,6 @@ extern "C" int odwf_net_create(odwf_t* h, int channels, odwf_net_t** out) {
     n->h = h;
     n->C = channels;
     if (const char* e = std::getenv("ODWF_TCGEN05")) n->use_tc = (e[0] == '1');
-    if (const char* e = std::getenv("ODWF_NET_PF")) n->mt_form = (e[0] == '1') ? 1 : (e[0] == '2' ? 2 : 0);
     if (const char* e = std::getenv("ODWF_NET_OCC")) {
         int a = 1, b = 0;
         if (std::sscanf(e, "%d:%d", &a, &b) == 2) {

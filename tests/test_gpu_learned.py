@@ -194,16 +194,13 @@ def test_gcr_rejects_bad_basis_and_reports_noconv(env):
     assert st["status"] == binding.ODWF_ENOCONV and st["iters"] == 3 and st["true_residual"] > 1e-10
 
 
-@pytest.mark.parametrize("use_tc,pf,occ", [("1", "0", "4:4"), ("0", "0", "4:4"), ("1", "0", "1:5"),
-                                          ("1", "1", "4:4"), ("1", "2", "4:4")])
-def test_net_ns16_tensor_memory_layer(use_tc, pf, occ, monkeypatch):
+@pytest.mark.parametrize("use_tc,occ", [("1", "4:4"), ("0", "4:4"), ("1", "1:5")])
+def test_net_ns16_tensor_memory_layer(use_tc, occ, monkeypatch):
     """At Ns = 16 the 1 -> 2 layer (forward, and the first adjoint layer) runs on the fifth-generation
     tensor cores: tcgen05.mma with FP32 accumulators in tensor memory; ODWF_TCGEN05=0 selects the
-    mma.sync layer. Every launch form of the layers (register caps ODWF_NET_OCC, the 2 -> 1 layer's row
-    prefetch ODWF_NET_PF) against the oracle (BF16 tolerance 2e-2 outputs, 5e-2 weight gradients), and
+    mma.sync layer. Every launch form of the layers (register caps ODWF_NET_OCC) against the oracle (BF16 tolerance 2e-2 outputs, 5e-2 weight gradients), and
     the preconditioned solve meets the FP64 true residual."""
     monkeypatch.setenv("ODWF_TCGEN05", use_tc)
-    monkeypatch.setenv("ODWF_NET_PF", pf)
     monkeypatch.setenv("ODWF_NET_OCC", occ)
     from paper_1710_09621_gb300 import build
     build.build()
