@@ -811,6 +811,9 @@ def main():
         l24.set_gauge(U24d)
         del U24
         b24 = torch.from_numpy(inputs.gaussian_spinor5(D24, NS, inputs.seed_for(2, 100 + rank))).to(dev)
+        tune24 = None
+        if not args.no_tune:  # the launch choices of this lattice, as for the workload above
+            tune24 = [l for l in l24.autotune(args.prec).splitlines() if l.startswith("chosen")]
         l24.solve(b24, MASS, MASS, opts=opts)
         l24.profile(True)
         (_, st24), t24 = timed(lambda: l24.solve(b24, MASS, MASS, opts=opts))
@@ -828,7 +831,7 @@ def main():
             avg_s = ms / 1e3 / n
             k24.append({"kernel": kernel_name(key), "launches": n, "avg_us": avg_s * 1e6,
                         "gbs": alg_bytes(key, Vh24, NS) / avg_s / 1e9, "share_ms": ms})
-        extra["paper_lattice"] = {"dims": list(D24), "Ns": NS, "plaquette": plaq24,
+        extra["paper_lattice"] = {"dims": list(D24), "Ns": NS, "plaquette": plaq24, "autotune": tune24,
                                   "method": f"CGNE, inner {args.prec}, FP64 reliable updates",
                                   "seconds": t24, "iters": st24["iters"], "true_residual": st24["true_residual"],
                                   "gflops": st24["iters"] * Vh24 * NS * CG_ITER_FLOPS / t24 / 1e9,
