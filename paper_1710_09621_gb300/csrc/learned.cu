@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(128, MINB) k_net_layer12_tc(NetLayerArgs a) {
                               smem_desc(Bsm + k * 2 * 128, 128, 1024), idesc, k > 0 ? 1u : 0u);
             umma_commit(bar);
         }
-        // one thread waits (bounded) and the CTA follows its verdict, so that the warp-collective
+        // one thread waits (bounded) and the CTA follows its outcome, so that the warp-collective
         // accumulator loads below run in every warp or in none
         if (tid == 0) {
             const bool done = tc_mbar_wait_bounded(bar, phase);
