@@ -1545,7 +1545,8 @@ int schur_finish(odwf_s* h, const SCoef* c, void* x, double bnorm2, double* res,
     // x == nullptr: the solution stays in ws.x_e / ws.x_o
     if (x && (rc = launch_unpack5(h, w.x_e, w.x_o, (double*)x, ST_DOUBLE, 0, st))) return rc;
     if ((rc = read_state(h, st))) return rc;
-    *res = std::sqrt((h->state_host->result[0] + h->state_host->result[1]) / bnorm2);
+    // b = 0: x = 0 solves the system exactly (the iteration never started)
+    *res = bnorm2 > 0.0 ? std::sqrt((h->state_host->result[0] + h->state_host->result[1]) / bnorm2) : 0.0;
     return ODWF_OK;
 }
 

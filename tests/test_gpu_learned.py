@@ -183,6 +183,18 @@ def test_gcr_solve(env, which, truncate):
           f"{st['reliable_updates']} cycles")
 
 
+def test_zero_rhs(env):
+    """b = 0: the network-preconditioned CGNE and GCR return x = 0 with no iteration and no error."""
+    binding, lat, op, U, om = env
+    net = binding.Net(lat, 2)
+    z = torch.zeros(lat.shape5, dtype=torch.complex128, device="cuda")
+    x, st = net.solve(z, M1, M2, opts=binding.solve_opts(tol=1e-10, prec="single", delta=1e-3))
+    assert torch.count_nonzero(x).item() == 0 and st["iters"] == 0 and st["true_residual"] == 0.0
+    x, st = lat.solve_gcr(z, M1, M2, net=net, nvec=8, opts=binding.solve_opts(tol=1e-10, prec="single"))
+    assert torch.count_nonzero(x).item() == 0 and st["iters"] == 0
+    net.close()
+
+
 def test_gcr_rejects_bad_basis_and_reports_noconv(env):
     binding, lat, op, U, om = env
     b = torch.from_numpy(inputs.gaussian_spinor5(DIMS, NS, 52)).cuda()
