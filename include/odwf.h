@@ -257,7 +257,8 @@ int odwf_net_apply(odwf_net_t* net, double m1, double m2, const void* r, void* o
 /* Training pairs (r_i, e_i = S^{-1} r_i): r_i are 5D ABI fields (even sites used); if e is NULL the
  * library solves for e_i itself (FP32 CGNE with FP64 reliable updates to tol), except when the loss
  * selected beforehand is ODWF_NET_LOSS_RESIDUAL, which never reads e_i: then no solve runs, and a later
- * switch to ODWF_NET_LOSS_ERROR makes odwf_net_loss_grad / odwf_net_train return ODWF_EINVAL. */
+ * switch to ODWF_NET_LOSS_ERROR makes odwf_net_loss_grad / odwf_net_train return ODWF_EINVAL. An r_i that
+ * vanishes (or is not finite) on the even sites is rejected with ODWF_EINVAL. */
 int odwf_net_set_pairs(odwf_net_t* net, double m1, double m2, int npairs, const void* const* r,
                        const void* const* e, double tol, void* stream);
 /* Training loss of odwf_net_loss_grad / odwf_net_train: ODWF_NET_LOSS_ERROR (default),

@@ -1356,18 +1356,21 @@ extern "C" int odwf_net_apply(odwf_net_t* n, double m1, double m2, const void* r
 // Training pairs: r_i (ABI 5D fields, even sites used) and, when e == NULL, e_i = S^{-1} r_i from
 // the library's own solver (FP32 inner CGNE with FP64 reliable updates, tolerance tol); otherwise
 // the given e_i. Replaces earlier pairs.
-extern "C" int odwf_net_set_pairs(odwf_net_t* n, double m1, double m2, int npairs, const void* const* r,
-                                  const void* const* e, double tol, void* stream) {
-    if (!n || npairs < 1 || !r) return ODWF_EINVAL;
+static void clear_pairs(odwf_net_s* n) {
+    for (float* p : n->pairs) cudaFree(p);
+    n->pairs.clear();
+    n->pair_ne.clear();
+    n->pair_nr.clear();
+}
+
+static int set_pairs_impl(odwf_net_t* n, double m1, double m2, int npairs, const void* const* r,
+                          const void* const* e, double tol, void* stream) {
     odwf_s* h = n->h;
     cudaStream_t st = (cudaStream_t)stream;
     int rc = ensure_workspace(h, ST_DOUBLE);
     if (rc) return rc;
     if ((rc = net_set_masses(n, m1, m2))) return rc;
-    for (float* p : n->pairs) cudaFree(p);
-    n->pairs.clear();
-    n->pair_ne.clear();
-    n->pair_nr.clear();
+    clear_pairs(n);
     odwf_solve_opts so{tol, 100000, ODWF_PREC_SINGLE, 0.01, 0.0};
     for (int i = 0; i < npairs; ++i) {
         float *rf = nullptr, *ef = nullptr;
@@ -1395,10 +1398,21 @@ extern "C" int odwf_net_set_pairs(odwf_net_t* n, double m1, double m2, int npair
         if ((rc = cuda_check(h, cudaMemcpyAsync(&hs, h->state, sizeof(CGState), cudaMemcpyDeviceToHost, st), "D2H")))
             return rc;
         if ((rc = cuda_check(h, cudaStreamSynchronize(st), "sync"))) return rc;
+        if (!(hs.result[1] > 0.0) || !std::isfinite(hs.result[1]))
+            return set_err(h, ODWF_EINVAL, "a training vector r_i is zero or not finite on the even sites");
         n->pair_ne.push_back(hs.result[0]);
         n->pair_nr.push_back(hs.result[1]);
     }
     return ODWF_OK;
+}
+
+extern "C" int odwf_net_set_pairs(odwf_net_t* n, double m1, double m2, int npairs, const void* const* r,
+                                  const void* const* e, double tol, void* stream) {
+    if (!n || npairs < 1 || !r) return ODWF_EINVAL;
+    const int rc = set_pairs_impl(n, m1, m2, npairs, r, e, tol, stream);
+    // on any error no partial pair set stays behind (the loss indexes the pairs' norms by pair)
+    if (rc != ODWF_OK) clear_pairs(n);
+    return rc;
 }
 
 extern "C" int odwf_net_set_loss(odwf_net_t* n, int mode) {

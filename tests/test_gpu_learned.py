@@ -195,6 +195,25 @@ def test_zero_rhs(env):
     net.close()
 
 
+def test_zero_training_vector_rejected(env):
+    """A training vector that vanishes is refused (ODWF_EINVAL) and leaves no partial pair set; valid
+    pairs set afterwards train as usual."""
+    binding, lat, op, U, om = env
+    net = binding.Net(lat, 2)
+    net.set_loss("residual")
+    good = torch.from_numpy(inputs.gaussian_spinor5(DIMS, NS, 80)).cuda()
+    z = torch.zeros(lat.shape5, dtype=torch.complex128, device="cuda")
+    with pytest.raises(binding.OdwfError) as ei:
+        net.set_pairs([good, z], M1, M2)
+    assert ei.value.code == binding.ODWF_EINVAL
+    with pytest.raises(binding.OdwfError):
+        net.loss_grad()  # no pairs stored
+    net.set_pairs([good], M1, M2)
+    losses = net.train(3, 2e-3)
+    assert np.all(np.isfinite(losses))
+    net.close()
+
+
 def test_gcr_rejects_bad_basis_and_reports_noconv(env):
     binding, lat, op, U, om = env
     b = torch.from_numpy(inputs.gaussian_spinor5(DIMS, NS, 52)).cuda()
